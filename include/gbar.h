@@ -1,0 +1,166 @@
+/*
+ * gbar.h -- C ABI of the GB300 (sm_103a) library for parallel
+ * acceptance-rejection (AR) selection of the next reaction to occur in the
+ * Stochastic Simulation Algorithm (Neri & Mestivier, 2014).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Pointers named d_* are caller-owned DEVICE memory; h_* are host memory.
+ *   The library never allocates in these calls and keeps no pointer after
+ *   the call returns (the network handle of the SSA calls is the exception:
+ *   it owns device copies of the network until ssa_net_destroy).
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Every call is asynchronous with respect to the host: it
+ *   validates its arguments, enqueues kernels and returns.
+ * - Return value: AR_OK (0) or a negative AR_ERR_* code for an error found
+ *   on the host before anything was enqueued (AR_ERR_CUDA: a launch failed;
+ *   cudaGetLastError() has been consumed and its code is returned by
+ *   ar_last_cuda_error()).
+ * - Conditions found on the device are OR-ed into the caller's uint32_t
+ *   status word(s) as AR_STATUS_* bits; the caller zeroes them beforehand
+ *   and reads them back when it wants them.
+ * - Indices are 0-based.  The rejection sentinel is M (the paper's M+1,
+ *   Section "Implementation", made 0-based).
+ * - dtype: AR_F32 or AR_F64 propensities.  cmp: AR_CMP_F32 (comparison in
+ *   FP32, bulk fast path) or AR_CMP_F64.
+ *
+ * The random stream (bit-exact contract, Philox4x32-10, Salmon et al. SC'11)
+ * -----------------------------------------------------------------------
+ * key = (seed mod 2^32, seed / 2^32).  Trial t (t = 0, 1, ...) of selection s
+ * of realization b reads the Philox block of counter (t/2, s, b, 0) and, in
+ * it, words 2(t mod 2) (candidate) and 2(t mod 2)+1 (uniform):
+ *     j = floor(w_a * M / 2^32)
+ *     FP64 comparison: accept iff fl64((w_b * 2^-32) * T) < alpha_j
+ *     FP32 comparison: accept iff fl32((floor(w_b/2^8) * 2^-24) * fl32(T))
+ *                                  < fl32(alpha_j)
+ * A selection returns the candidate of its first accepted trial, or M (and
+ * AR_STATUS_TRIAL_CAP) when trials 0 .. trial_cap-1 all reject.  This is the
+ * sequential AR method of Section "A GPU acceptance-rejection algorithm"
+ * (choose j at random and u in [0,T) until u < alpha_j) with T = max_j
+ * alpha_j (Section "Election step"; experiments' T_w = w max alpha, w = 1).
+ * Conditioned on acceptance the law is alpha_j / sum(alpha) up to the
+ * 2^-32 candidate lattice and the 2^-24 / 2^-32 uniform lattice.
+ */
+#ifndef GBAR_H
+#define GBAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define AR_OK 0
+#define AR_ERR_ARG (-1)       /* bad size, null pointer or enum value     */
+#define AR_ERR_ALIGN (-2)     /* a pointer lacks its required alignment   */
+#define AR_ERR_CUDA (-3)      /* a CUDA call failed (see ar_last_cuda_error) */
+#define AR_ERR_WORKSPACE (-4) /* workspace too small                       */
+#define AR_ERR_UNSUPPORTED (-5) /* size beyond what this build supports   */
+
+/* ---- device status bits ---------------------------------------------- */
+#define AR_STATUS_BAD_ALPHA 1u  /* a propensity is NaN, +-inf or < 0       */
+#define AR_STATUS_ALL_ZERO 2u   /* every propensity is 0 (paper's rejection) */
+#define AR_STATUS_TRIAL_CAP 4u  /* a selection hit trial_cap; sentinel M   */
+#define AR_STATUS_BAD_BOUND 8u  /* bound NaN, inf, < 0 (or inf in FP32)    */
+#define AR_STATUS_ABSORBED 16u  /* SSA realization reached a0 = 0          */
+#define AR_STATUS_TIMEOUT 32u   /* a bounded device wait gave up           */
+
+typedef enum { AR_F32 = 0, AR_F64 = 1 } ar_dtype;
+typedef enum { AR_CMP_F32 = 0, AR_CMP_F64 = 1 } ar_cmp;
+
+/* Selection bookkeeping (Section "Assessing the qualities": rejection rate).
+ * trials = sum over selections of trials consumed (t_accept + 1, or
+ * trial_cap when capped); accepted / capped = counts.  Added atomically. */
+typedef struct {
+    uint64_t trials;
+    uint64_t accepted;
+    uint64_t capped;
+} ar_stats;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int ar_version(void);
+/* Last CUDA error code seen by a call that returned AR_ERR_CUDA. */
+int ar_last_cuda_error(void);
+
+/* ---------------------------------------------------------------------
+ * ar_bound -- threshold and total propensity of one vector.
+ * Paper: T = max_j alpha_j (Section "Election step"; experiments T_w with
+ * w = 1, Section "Quality of the selection"); alpha_0 = sum_j alpha_j
+ * (Section "The Stochastic Simulation Algorithm").
+ *   d_alpha      [M] FP32 or FP64 (dtype), 4- or 8-byte aligned.
+ *   d_bound_sum  [2] double out: {max (exact), sum (FP64-grade: within
+ *                (M + 8) * 2^-53 * sum of the exact sum)}.
+ *   d_status     OR-ed with BAD_ALPHA (any NaN/inf/negative; -0 is 0) or
+ *                ALL_ZERO (max = 0, including M = 0).  Outputs are
+ *                unspecified when BAD_ALPHA is set.
+ *   d_work       scratch of ar_bound_workspace_size(M) bytes (may be NULL
+ *                when that size is 0), 16-byte aligned; the call clears
+ *                what it needs.
+ * Errors: AR_ERR_ARG (M < 0, null pointers, bad dtype), AR_ERR_ALIGN,
+ * AR_ERR_WORKSPACE.
+ * ------------------------------------------------------------------- */
+size_t ar_bound_workspace_size(int64_t M, int dtype);
+int ar_bound(const void *d_alpha, int dtype, int64_t M, double *d_bound_sum,
+             uint32_t *d_status, void *d_work, size_t work_bytes, void *stream);
+
+/* ---------------------------------------------------------------------
+ * ar_select_k -- K independent selections from one propensity vector
+ * (Section "A GPU acceptance-rejection algorithm": select the K next
+ * reactions; the paper's K parallel realizations sharing one D in its
+ * quality experiment, Section "Test and validation").
+ *   d_alpha      [M] FP32/FP64.  1 <= M < 2^31 (M = 0: every index is 0).
+ *   d_bound      NULL: the kernel uses T = max_j alpha_j, computed in each
+ *                CTA from its shared-memory copy (requires M *
+ *                element size <= ar_select_k_smem_limit()); else a device
+ *                double T >= max alpha (T = w max, w >= 1 keeps the law).
+ *   K            number of selections, 0 <= K, sel_offset + K <= 2^32.
+ *   seed, sel_offset, realization  the random stream (see top).  Output i
+ *                is selection s = sel_offset + i.
+ *   cmp          AR_CMP_F32 or AR_CMP_F64.
+ *   trial_cap    1 <= trial_cap <= 2^32 trials per selection.
+ *   d_idx        [K] int32 out, selected indices (M = sentinel).
+ *   d_stats      nullable ar_stats accumulator.
+ *   d_status     OR-ed with ALL_ZERO, TRIAL_CAP, BAD_BOUND.
+ * ------------------------------------------------------------------- */
+size_t ar_select_k_smem_limit(void);
+int ar_select_k(const void *d_alpha, int dtype, int64_t M, const double *d_bound,
+                int64_t K, uint64_t seed, uint64_t sel_offset, uint32_t realization,
+                int cmp, uint64_t trial_cap, int32_t *d_idx, ar_stats *d_stats,
+                uint32_t *d_status, void *stream);
+
+/* ---------------------------------------------------------------------
+ * ar_select_batched -- many realizations with uneven M_b and K_b in one
+ * persistent launch (Section "A GPU acceptance-rejection algorithm": K
+ * realizations as K blocks; the text's extension to M beyond one block).
+ * Realization b owns alpha_cat[offsets[b] .. offsets[b+1]) and writes
+ * K_b = out_offsets[b+1] - out_offsets[b] indices at d_idx[out_offsets[b]].
+ * Its bound is its own maximum, computed in the kernel; its Philox
+ * realization id is realization_base + b; its selection ids are
+ * sel_offset + 0 .. K_b-1.
+ *   d_alpha_cat      FP32 or FP64 (dtype).
+ *   d_offsets        [B+1] int64, non-decreasing, offsets[0] = 0.
+ *   d_out_offsets    [B+1] int64, non-decreasing, out_offsets[0] = 0.
+ *   d_bound_sum      [B][2] double out: {max, sum} per realization.
+ *   plan             nullable tuning handle from ar_plan_create (NULL =
+ *                    defaults).
+ *   d_work           scratch of ar_select_batched_workspace_size(B) bytes,
+ *                    16-byte aligned; cleared by the call.
+ *   d_idx, d_stats, d_status   as in ar_select_k (status also collects
+ *                    BAD_ALPHA and ALL_ZERO of any realization).
+ * ------------------------------------------------------------------- */
+typedef struct ar_plan ar_plan;
+size_t ar_select_batched_workspace_size(int64_t B);
+int ar_select_batched(const void *d_alpha_cat, int dtype, const int64_t *d_offsets,
+                      const int64_t *d_out_offsets, int64_t B, uint64_t seed,
+                      uint64_t sel_offset, uint32_t realization_base, int cmp,
+                      uint64_t trial_cap, const ar_plan *plan, double *d_bound_sum,
+                      int32_t *d_idx, ar_stats *d_stats, uint32_t *d_status,
+                      void *d_work, size_t work_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBAR_H */

@@ -1,0 +1,206 @@
+"""Thin Python binding of libgbar.so (the C ABI declared in include/gbar.h).
+
+Functions keep the C names and argument order; device buffers are passed as
+CUDA torch tensors (PyTorch is only the device-memory and stream provider).
+Every step of the selection runs in the library's kernels: there is no
+Python or CPU fallback, and calling anything here without the built library
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgbar.so")
+
+AR_OK = 0
+AR_ERR_ARG = -1
+AR_ERR_ALIGN = -2
+AR_ERR_CUDA = -3
+AR_ERR_WORKSPACE = -4
+AR_ERR_UNSUPPORTED = -5
+_ERR_NAMES = {AR_ERR_ARG: "AR_ERR_ARG", AR_ERR_ALIGN: "AR_ERR_ALIGN", AR_ERR_CUDA: "AR_ERR_CUDA",
+              AR_ERR_WORKSPACE: "AR_ERR_WORKSPACE", AR_ERR_UNSUPPORTED: "AR_ERR_UNSUPPORTED"}
+
+AR_STATUS_BAD_ALPHA = 1
+AR_STATUS_ALL_ZERO = 2
+AR_STATUS_TRIAL_CAP = 4
+AR_STATUS_BAD_BOUND = 8
+AR_STATUS_ABSORBED = 16
+AR_STATUS_TIMEOUT = 32
+
+AR_F32 = 0
+AR_F64 = 1
+AR_CMP_F32 = 0
+AR_CMP_F64 = 1
+
+_lock = threading.Lock()
+_lib = None
+
+_vp, _i64, _u64, _u32, _int, _sz = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64,
+                                     ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t)
+
+# name -> (restype, argtypes); mirrors include/gbar.h
+SIGNATURES = {
+    "ar_version": (_int, []),
+    "ar_last_cuda_error": (_int, []),
+    "ar_bound_workspace_size": (_sz, [_i64, _int]),
+    "ar_bound": (_int, [_vp, _int, _i64, _vp, _vp, _vp, _sz, _vp]),
+    "ar_select_k_smem_limit": (_sz, []),
+    "ar_select_k": (_int, [_vp, _int, _i64, _vp, _i64, _u64, _u64, _u32, _int, _u64, _vp, _vp,
+                           _vp, _vp]),
+    "ar_select_batched_workspace_size": (_sz, [_i64]),
+    "ar_select_batched": (_int, [_vp, _int, _vp, _vp, _i64, _u64, _u64, _u32, _int, _u64, _vp,
+                                 _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+}
+
+
+class GbarError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libgbar.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise GbarError(f"{LIB_PATH} is missing: build it with "
+                                    "paper_1404_0027_gb300.build.build() (needs nvcc)")
+                L = ctypes.CDLL(LIB_PATH)
+                for name, (res, args) in SIGNATURES.items():
+                    f = getattr(L, name)
+                    f.restype = res
+                    f.argtypes = args
+                _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != AR_OK:
+        extra = ""
+        if rc == AR_ERR_CUDA:
+            extra = f" (cudaError {lib().ar_last_cuda_error()})"
+        raise GbarError(f"{what} returned {_ERR_NAMES.get(rc, rc)}{extra}")
+
+
+def _dev(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise GbarError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise GbarError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise GbarError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return AR_F32
+    if t.dtype == torch.float64:
+        return AR_F64
+    raise GbarError("propensities must be float32 or float64")
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# --------------------------------------------------------------------------
+# C-ABI mirrors
+# --------------------------------------------------------------------------
+def ar_bound_workspace_size(M: int, dtype: int) -> int:
+    return int(lib().ar_bound_workspace_size(M, dtype))
+
+
+def ar_bound(alpha, bound_sum, status, work=None, stream=None):
+    """alpha [M] f32/f64 -> bound_sum [2] f64 (max, sum); status u32[1] |= bits."""
+    nbytes = 0 if work is None else work.numel() * work.element_size()
+    _check(lib().ar_bound(_dev(alpha, name="alpha"), _dtype_code(alpha), alpha.numel(),
+                          _dev(bound_sum, torch.float64, "bound_sum"),
+                          _dev(status, torch.int32, "status"), _dev(work, name="work"), nbytes,
+                          _stream(stream)), "ar_bound")
+
+
+def ar_select_k_smem_limit() -> int:
+    return int(lib().ar_select_k_smem_limit())
+
+
+def ar_select_k(alpha, bound, K, seed, sel_offset, realization, cmp, trial_cap, idx, stats,
+                status, stream=None):
+    """K selections from alpha into idx int32[K]; bound f64[>=1] tensor or None."""
+    _check(lib().ar_select_k(_dev(alpha, name="alpha"), _dtype_code(alpha), alpha.numel(),
+                             _dev(bound, torch.float64, "bound"), K, seed, sel_offset,
+                             realization, cmp, trial_cap, _dev(idx, torch.int32, "idx"),
+                             _dev(stats, torch.int64, "stats"), _dev(status, torch.int32, "status"),
+                             _stream(stream)), "ar_select_k")
+
+
+def ar_select_batched_workspace_size(B: int) -> int:
+    return int(lib().ar_select_batched_workspace_size(B))
+
+
+def ar_select_batched(alpha_cat, offsets, out_offsets, seed, sel_offset, realization_base, cmp,
+                      trial_cap, plan, bound_sum, idx, stats, status, work, stream=None):
+    B = offsets.numel() - 1
+    nbytes = 0 if work is None else work.numel() * work.element_size()
+    _check(lib().ar_select_batched(
+        _dev(alpha_cat, name="alpha_cat"), _dtype_code(alpha_cat),
+        _dev(offsets, torch.int64, "offsets"), _dev(out_offsets, torch.int64, "out_offsets"), B,
+        seed, sel_offset, realization_base, cmp, trial_cap,
+        None if plan is None else ctypes.c_void_p(plan),
+        _dev(bound_sum, torch.float64, "bound_sum"), _dev(idx, torch.int32, "idx"),
+        _dev(stats, torch.int64, "stats"), _dev(status, torch.int32, "status"),
+        _dev(work, name="work"), nbytes, _stream(stream)), "ar_select_batched")
+
+
+# --------------------------------------------------------------------------
+# Convenience wrappers that allocate their outputs
+# --------------------------------------------------------------------------
+def bound(alpha, stream=None):
+    """-> (bound_sum f64[2] tensor, status i32[1] tensor)."""
+    dev = alpha.device
+    out = torch.empty(2, dtype=torch.float64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = ar_bound_workspace_size(alpha.numel(), _dtype_code(alpha))
+    work = torch.empty(max(ws, 16), dtype=torch.uint8, device=dev) if ws else None
+    ar_bound(alpha, out, st, work, stream)
+    return out, st
+
+
+def select_k(alpha, K, seed=1, sel_offset=0, realization=0, cmp=AR_CMP_F32, bound=None,
+             trial_cap=1 << 20, stream=None):
+    """-> (idx int32[K], stats int64[3] = trials/accepted/capped, status int32[1])."""
+    dev = alpha.device
+    idx = torch.empty(K, dtype=torch.int32, device=dev)
+    stats = torch.zeros(3, dtype=torch.int64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    ar_select_k(alpha, bound, K, seed, sel_offset, realization, cmp, trial_cap, idx, stats, st,
+                stream)
+    return idx, stats, st
+
+
+def select_batched(alpha_cat, offsets, out_offsets, seed=1, sel_offset=0, realization_base=0,
+                   cmp=AR_CMP_F32, trial_cap=1 << 20, plan=None, stream=None):
+    """-> (bound_sum f64[B,2], idx int32[sum K], stats int64[3], status int32[1])."""
+    dev = alpha_cat.device
+    B = offsets.numel() - 1
+    bs = torch.empty((B, 2), dtype=torch.float64, device=dev)
+    idx = torch.empty(int(out_offsets[-1].item()), dtype=torch.int32, device=dev)
+    stats = torch.zeros(3, dtype=torch.int64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    work = torch.empty(max(ar_select_batched_workspace_size(B), 16), dtype=torch.uint8,
+                       device=dev)
+    ar_select_batched(alpha_cat, offsets, out_offsets, seed, sel_offset, realization_base, cmp,
+                      trial_cap, plan, bs, idx, stats, st, work, stream)
+    return bs, idx, stats, st

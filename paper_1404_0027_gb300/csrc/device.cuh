@@ -1,0 +1,204 @@
+// Device building blocks shared by the GB300 kernels: the counter-based
+// random stream, the AR trial, warp/block reductions and the exact
+// fixed-point accumulation used for the FP64-grade total propensity.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gbar.h"
+
+namespace gbar {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of
+//   (x0,x1,x2,x3) -> (hi(B*x2)^x1^k0, lo(B*x2), hi(A*x0)^x3^k1, lo(A*x0))
+// with A = 0xD2511F53, B = 0xCD9E8D57 and the key advanced by the Weyl
+// increments (0x9E3779B9, 0xBB67AE85) after every round.  Generated in
+// registers: the paper's K x M uniform array in global memory (Section
+// "Materials", Discussion) is never materialised.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo_a = 0xD2511F53u * c.x;
+    const uint32_t hi_a = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo_b = 0xCD9E8D57u * c.z;
+    const uint32_t hi_b = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi_b ^ c.y ^ k0, lo_b, hi_a ^ c.w ^ k1, lo_a);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Candidate index of a trial: floor(w * M / 2^32) (uniform over 0..M-1 up to
+// a 2^-32 preimage lattice).  Requires M < 2^31.
+__device__ __forceinline__ uint32_t candidate(uint32_t w, uint32_t M) {
+  return __umulhi(w, M);
+}
+
+// The AR acceptance test u * T < alpha_j with u in [0,1) (Section "A GPU
+// acceptance-rejection algorithm"; strict '<' so that alpha_j = 0 is never
+// chosen).  One IEEE round-to-nearest multiply, no contraction.
+__device__ __forceinline__ bool accept_f32(uint32_t w, float T, float a) {
+  const float u = __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
+  return __fmul_rn(u, T) < a;
+}
+__device__ __forceinline__ bool accept_f64(uint32_t w, double T, double a) {
+  const double u = __dmul_rn(__uint2double_rn(w), 0x1p-32);
+  return __dmul_rn(u, T) < a;
+}
+
+// ---------------------------------------------------------------------------
+// Warp / block reductions.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t warp_max_u32(uint32_t v) {
+  return __reduce_max_sync(kFull, v);
+}
+__device__ __forceinline__ int32_t warp_max_i32(int32_t v) {
+  return __reduce_max_sync(kFull, v);
+}
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ long long warp_max_i64(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const long long w = __shfl_xor_sync(kFull, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __fadd_rn(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 validity and maximum on bit patterns.  For non-negative IEEE values
+// the unsigned bit order is the value order, so the maximum is exact and
+// needs no floating-point unit.  A value is valid when it is +finite or -0:
+//   smax = max of the bits read as int32   (negative patterns drop out)
+//   umax = max of the bits read as uint32  (> 0x80000000 => negative value)
+// ---------------------------------------------------------------------------
+struct MaxF32 {
+  int32_t smax = INT32_MIN;
+  uint32_t umax = 0;
+  __device__ __forceinline__ void add(uint32_t bits) {
+    smax = max(smax, (int32_t)bits);
+    umax = max(umax, bits);
+  }
+  __device__ __forceinline__ bool bad() const {
+    return smax >= 0x7f800000 || umax > 0x80000000u;
+  }
+  __device__ __forceinline__ uint32_t value_bits() const {
+    return smax < 0 ? 0u : (uint32_t)smax;
+  }
+};
+struct MaxF64 {
+  long long smax = INT64_MIN;
+  unsigned long long umax = 0;
+  __device__ __forceinline__ void add(unsigned long long bits) {
+    smax = max(smax, (long long)bits);
+    umax = max(umax, bits);
+  }
+  __device__ __forceinline__ bool bad() const {
+    return smax >= 0x7ff0000000000000ll || umax > 0x8000000000000000ull;
+  }
+  __device__ __forceinline__ unsigned long long value_bits() const {
+    return smax < 0 ? 0ull : (unsigned long long)smax;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Exact fixed-point accumulation of non-negative FP32 values given the
+// biased exponent e_ref of their maximum (GB300 runs FP64 adds at a small
+// fraction of its integer rate, so the per-element work stays in integers):
+//   value = m * 2^(e - 150), m the 24-bit significand, e >= 1 the exponent;
+//   d = e_ref - e >= 0;  d <= 24: a1 += m << (24 - d)   (unit 2^(e_ref-174))
+//                        d <= 49: a2 += m << (49 - d)   (unit 2^(e_ref-199))
+//                        else     a3 += value (FP32; each term < 2^-48 max)
+// Terms are < 2^48, so a1 and a2 stay exact for up to 2^15 elements; they
+// are order-independent integers.  The result, rounded once to FP64 per
+// window, is within 3 * 2^-53 * sum + 2^-60 * max of the exact sum.
+// ---------------------------------------------------------------------------
+struct FxSum {
+  unsigned long long a1 = 0, a2 = 0;
+  float a3 = 0.f;
+  __device__ __forceinline__ void add(uint32_t bits, int e_ref) {
+    bits &= 0x7fffffffu;
+    int e = (int)(bits >> 23);
+    uint32_t m = bits & 0x7fffffu;
+    if (e) m |= 0x800000u; else e = 1;
+    const int d = e_ref - e;
+    if (d <= 24) {
+      a1 += (unsigned long long)m << (24 - d);
+    } else if (d <= 49) {
+      a2 += (unsigned long long)m << (49 - d);
+    } else {
+      a3 = __fadd_rn(a3, __uint_as_float(bits));
+    }
+  }
+  __device__ __forceinline__ void merge(const FxSum& o) {
+    a1 += o.a1;
+    a2 += o.a2;
+    a3 = __fadd_rn(a3, o.a3);
+  }
+  __device__ __forceinline__ void warp_reduce() {
+    a1 = warp_sum_u64(a1);
+    a2 = warp_sum_u64(a2);
+    a3 = warp_sum_f32(a3);
+  }
+  // e_ref here is max(biased exponent of the maximum, 1).
+  __device__ __forceinline__ double to_double(int e_ref) const {
+    const double s1 = __hiloint2double((e_ref - 174 + 1023) << 20, 0);
+    const double s2 = __hiloint2double((e_ref - 199 + 1023) << 20, 0);
+    const double hi = __dmul_rn(__ull2double_rn(a1), s1);
+    const double mid = __dmul_rn(__ull2double_rn(a2), s2);
+    return __dadd_rn(__dadd_rn(hi, mid), (double)a3);
+  }
+};
+
+__device__ __forceinline__ int fx_eref(uint32_t max_bits) {
+  const int e = (int)((max_bits & 0x7fffffffu) >> 23);
+  return e < 1 ? 1 : e;
+}
+
+// Bounded wait on an mbarrier phase (no unbounded spin anywhere): returns
+// false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
+  for (uint32_t i = 0; i < limit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity), "r"(100000u)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+}  // namespace gbar

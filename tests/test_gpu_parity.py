@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Indices, trial counts and maxima must be bit-exact; the total propensity must
+lie within 2 (M + 8) 2^-53 sum of the oracle's FP64 index-order sum (the
+oracle's own rounding is at most (M - 1) 2^-53 sum, the library's at most
+(M + 8) 2^-53 sum of the exact value).
+"""
+import numpy as np
+import pytest
+
+from paper_1404_0027_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+CAP = 1 << 20
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    from paper_1404_0027_gb300 import build
+    build.build()
+    from paper_1404_0027_gb300 import binding
+    binding.lib()
+    assert torch.cuda.is_available()
+    return binding
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _sum_tol(a, total):
+    return 2.0 * (a.size + 8) * 2.0 ** -53 * abs(total)
+
+
+# ---------------------------------------------------------------- ar_bound
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("M", [0, 1, 7, 1024, 4095, 4096, 4097, 8191, 8192, 8193, 100_003, 1 << 20])
+def test_bound_parity(gb, orc, dtype, M):
+    a = W.wide_range(M, seed=M + 3).astype(dtype) if M else np.zeros(0, dtype=dtype)
+    out, st = gb.bound(_t(a))
+    mx, sm, ost = orc.bound(a)
+    got = out.cpu().numpy()
+    assert got[0] == mx
+    assert abs(got[1] - sm) <= _sum_tol(a, sm)
+    assert int(st.item()) == ost
+
+
+@pytest.mark.parametrize("make", [W.plain_uniform, W.skewed, lambda: W.gaussian_paper(1024)])
+def test_bound_workloads(gb, orc, make):
+    a = make()
+    out, st = gb.bound(_t(a))
+    mx, sm, ost = orc.bound(a)
+    got = out.cpu().numpy()
+    assert got[0] == mx and abs(got[1] - sm) <= _sum_tol(a, sm) and int(st.item()) == ost
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("bad", [np.nan, -1.0, np.inf])
+@pytest.mark.parametrize("M", [100, 50_000])
+def test_bound_flags(gb, orc, dtype, bad, M):
+    a = W.plain_uniform(M).astype(dtype)
+    a[M // 3] = bad
+    _, st = gb.bound(_t(a))
+    assert int(st.item()) & gb.AR_STATUS_BAD_ALPHA
+    z = np.zeros(M, dtype=dtype)
+    z[5] = -0.0
+    out, st = gb.bound(_t(z))
+    assert int(st.item()) == gb.AR_STATUS_ALL_ZERO and out.cpu().numpy().tolist() == [0.0, 0.0]
+
+
+# ------------------------------------------------------------- ar_select_k
+def _check_select(gb, orc, a, K, cmp, fused, seed=1, sel_offset=0, realization=0,
+                  bound_value=None, cap=CAP):
+    import torch
+    T = orc.bound(a)[0] if bound_value is None else bound_value
+    bound = None if fused else torch.tensor([T], dtype=torch.float64, device="cuda")
+    idx, stats, st = gb.select_k(_t(a), K, seed=seed, sel_offset=sel_offset,
+                                 realization=realization, cmp=cmp, bound=bound, trial_cap=cap)
+    oidx, ostats, ost = orc.select_ar(a, K, seed=seed, sel_offset=sel_offset,
+                                      realization=realization, cmp=cmp, bound_value=T,
+                                      trial_cap=cap, nthreads=8)
+    g = idx.cpu().numpy()
+    mism = np.flatnonzero(g != oidx)
+    assert mism.size == 0, f"{mism.size} mismatches, first at {mism[:5]}: {g[mism[:5]]} vs {oidx[mism[:5]]}"
+    np.testing.assert_array_equal(stats.cpu().numpy().astype(np.uint64), ostats)
+    assert int(st.item()) == ost
+
+
+@pytest.mark.parametrize("cmp", [0, 1])
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_select_plain(gb, orc, cmp, fused, dtype):
+    _check_select(gb, orc, W.plain_uniform().astype(dtype), 1000, cmp, fused)
+
+
+@pytest.mark.parametrize("cmp", [0, 1])
+@pytest.mark.parametrize("K", [1, 33, 4097, 65536])
+def test_select_skewed(gb, orc, cmp, K):
+    _check_select(gb, orc, W.skewed(seed=200), K, cmp, fused=True, sel_offset=65536 * 3)
+
+
+@pytest.mark.parametrize("M", [1, 2, 3, 31, 32, 33, 1029, 40_000])
+@pytest.mark.parametrize("cmp", [0, 1])
+def test_select_sizes(gb, orc, M, cmp):
+    _check_select(gb, orc, W.skewed(M, seed=M), 3000, cmp, fused=(M <= 40_000),
+                  realization=M % 7)
+
+
+@pytest.mark.parametrize("cmp", [0, 1])
+def test_select_wide_range_l2_path(gb, orc, cmp):
+    """M = 2^20 does not fit shared memory: gathers from L2 with the bound
+    from ar_bound (the wide-dynamic-range workload, 12 decades)."""
+    a = W.wide_range(M=1 << 20)
+    _check_select(gb, orc, a, 20_000, cmp, fused=False)
+
+
+def test_select_trial_cap_and_bound_multiplier(gb, orc):
+    a = W.plain_uniform(100)
+    _check_select(gb, orc, a, 2000, 1, fused=False, bound_value=float(a.max()) * 1e6, cap=8)
+    _check_select(gb, orc, a, 2000, 0, fused=False, bound_value=float(a.max()) * 3.0)
+    _check_select(gb, orc, a, 2000, 0, fused=False, bound_value=float(a.max()) * 1e6,
+                  cap=(1 << 32))
+
+
+def test_select_degenerate(gb, orc):
+    import torch
+    z = np.zeros(40, dtype=np.float32)
+    _check_select(gb, orc, z, 100, 0, fused=True)
+    one = np.zeros(555, dtype=np.float32)
+    one[321] = 2.5
+    _check_select(gb, orc, one, 500, 0, fused=True)
+    _check_select(gb, orc, np.full(64, 3.0), 256, 1, fused=False)
+    for T in (float("nan"), -1.0, float("inf")):
+        _check_select(gb, orc, W.plain_uniform(16), 8, 1, fused=False, bound_value=T)
+    # K = 0 is a no-op; M = 0 returns the sentinel 0
+    idx, stats, st = gb.select_k(_t(np.zeros(0, dtype=np.float32)), 5)
+    assert idx.cpu().tolist() == [0] * 5 and int(st.item()) == gb.AR_STATUS_ALL_ZERO
+    idx, _, _ = gb.select_k(_t(W.plain_uniform(8)), 0)
+    assert idx.numel() == 0
+    with pytest.raises(gb.GbarError):
+        gb.select_k(_t(W.plain_uniform(8)), 4, sel_offset=(1 << 32) - 2)
+    with pytest.raises(gb.GbarError):
+        big = torch.zeros(60_000_000, dtype=torch.float32, device="cuda")
+        gb.select_k(big, 4)   # no bound and too large for shared memory
+
+
+# -------------------------------------------------------- ar_select_batched
+def _check_batched(gb, orc, bt, cmp=0, seed=1, sel_offset=0, realization_base=0):
+    bs, idx, stats, st = gb.select_batched(_t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets),
+                                           seed=seed, sel_offset=sel_offset,
+                                           realization_base=realization_base, cmp=cmp)
+    obs, oidx, ostats, ost = orc.select_batched(bt, seed=seed, sel_offset=sel_offset,
+                                                realization_base=realization_base, cmp=cmp,
+                                                nthreads=8)
+    g = idx.cpu().numpy()
+    mism = np.flatnonzero(g != oidx)
+    assert mism.size == 0, f"{mism.size} mismatches of {g.size}, first at {mism[:5]}"
+    gbs = bs.cpu().numpy()
+    np.testing.assert_array_equal(gbs[:, 0], obs[:, 0])
+    for b in range(bt.B):
+        a = bt.alpha[bt.offsets[b]:bt.offsets[b + 1]]
+        assert abs(gbs[b, 1] - obs[b, 1]) <= _sum_tol(a, obs[b, 1]), b
+    np.testing.assert_array_equal(stats.cpu().numpy().astype(np.uint64), ostats)
+    assert int(st.item()) == ost
+
+
+@pytest.mark.parametrize("cmp", [0, 1])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_batched_ragged(gb, orc, cmp, dtype):
+    vecs = [W.skewed(m, seed=m).astype(dtype) for m in (1, 2, 3, 5, 7, 64, 1000, 4099, 16384,
+                                                          20_000, 9, 1)]
+    vecs.append(np.zeros(33, dtype=dtype))
+    ks = [5, 0, 17, 1, 256, 300, 256, 1000, 64, 77, 3, 2, 9]
+    _check_batched(gb, orc, W.batch_from_vectors(vecs, ks), cmp=cmp, seed=7, sel_offset=11,
+                   realization_base=100)
+
+
+@pytest.mark.parametrize("cmp", [0, 1])
+def test_batched_uneven_small(gb, orc, cmp):
+    _check_batched(gb, orc, W.batched_uneven(B=300, seed=301, K=256), cmp=cmp)
+
+
+def test_batched_uneven_full(gb, orc):
+    """The full batched workload: 4096 realizations, M_b log-uniform in
+    [64, 16384], K_b = 256, FP32 comparison."""
+    _check_batched(gb, orc, W.batched_uneven())
