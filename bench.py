@@ -1,0 +1,498 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched AR selection hot path on GB300.
+
+One step = one ``ar_select_batched`` launch (bound/sum reduction, Philox
+trials, gathers, ballot compaction and output for every realization) on the
+batched-uneven workload: B = 4096 realizations, M_b log-uniform in
+[64, 16384], alpha FP32 Exponential(1), K_b = 256 selections each, FP32
+comparison.  The launch is replayed from a captured CUDA graph.  Inputs are
+rotated over several independently drawn batches whose total size exceeds
+the 129 MB L2, so every step streams its propensities from HBM.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the host cores instead (the comparison arm).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1404_0027_gb300 import workloads as W  # noqa: E402
+
+METRIC = "accepted selections/sec and HBM-roofline fraction, FP32-batched vs FP64-plain at TV<=1e-3"
+UNIT = "selections/s"
+B_REAL, K_B, M_LO, M_HI = 4096, 256, 64, 16384
+N_SLOTS = 6                      # 6 x ~52 MB > 129 MB L2
+SEED = 1
+PHILOX_IMAD_PER_BLOCK = 40       # 10 rounds x 2 multiplies x (hi + lo)
+IMAD_PER_SM_CLK = 64             # 32-bit integer multiply-add issue rate per SM per clock
+
+
+def workload_config():
+    return {"workload": f"batched-uneven: B={B_REAL} realizations, M_b log-uniform "
+                        f"[{M_LO},{M_HI}], alpha FP32 Exponential(1), K_b={K_B}, FP32 comparison, "
+                        "one persistent launch per step from a CUDA graph",
+            "B": B_REAL, "K_b": K_B, "M_range": [M_LO, M_HI], "cmp": "f32", "seed": SEED,
+            "l2": f"inputs rotated over {N_SLOTS} independently drawn batches "
+                  f"(~{N_SLOTS * 52} MB > 129 MB L2)"}
+
+
+def slot_seed(rank: int, slot: int) -> int:
+    return 300 + 1000 * rank + slot
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured", d
+    except Exception:
+        return 6800.0, "fallback", {}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1404_0027_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "source_hash")):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except OSError:
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 9:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        inside = [s for t, s in self.samples if t0 <= t <= t1]
+        if not inside and self.samples:
+            inside = [min(self.samples, key=lambda x: min(abs(x[0] - t0), abs(x[0] - t1)))[1]]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(s[1]) for s in inside if num(s[1]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in inside:
+            for n, v in zip(names, s[5:9]):
+                if v.strip().lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": num(inside[0][2]), "reasons": sorted(reasons),
+                "samples": len(inside), "power_w_max": max((num(s[3]) or 0) for s in inside)}
+
+
+def gpu_id_for(torch, dev) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        return vis.split(",")[dev.index or 0] if vis else str(dev.index or 0)
+
+
+def algorithmic_bytes(bt) -> int:
+    """alpha read once + both offset arrays read + indices and (max, sum) written."""
+    return 4 * int(bt.offsets[-1]) + 16 * (bt.B + 1) + 4 * int(bt.out_offsets[-1]) + 16 * bt.B
+
+
+# --------------------------------------------------------------------------
+# CPU oracle arm
+# --------------------------------------------------------------------------
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    bt = W.batched_uneven(B=B_REAL, seed=slot_seed(0, 0), m_lo=M_LO, m_hi=M_HI, K=K_B)
+    # size one step so that warmup + steps finish within about two minutes
+    t = time.perf_counter()
+    probe = W.batch_from_vectors([bt.alpha[bt.offsets[b]:bt.offsets[b + 1]] for b in range(64)],
+                                 [K_B] * 64)
+    oracle.select_batched(probe, seed=SEED, nthreads=cores)
+    per_real = (time.perf_counter() - t) / 64
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    nb = int(max(16, min(B_REAL, budget / max(per_real, 1e-9))))
+    sub = W.batch_from_vectors([bt.alpha[bt.offsets[b]:bt.offsets[b + 1]] for b in range(nb)],
+                               [K_B] * nb)
+    for _ in range(args.warmup):
+        oracle.select_batched(sub, seed=SEED, nthreads=cores)
+    t0 = time.perf_counter()
+    acc = 0
+    for _ in range(args.steps):
+        _, _, st, _ = oracle.select_batched(sub, seed=SEED, nthreads=cores)
+        acc += int(st[1])
+    dt = time.perf_counter() - t0
+    value = acc / dt
+    sample = (f"first {nb} of the {B_REAL} realizations of the batched workload per step "
+              f"({nb * K_B} selections, oracle C, FP32 comparison, OpenMP over selections)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "config": workload_config(),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def cpu_baseline_leg():
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    bt = W.batched_uneven(B=B_REAL, seed=slot_seed(0, 0), m_lo=M_LO, m_hi=M_HI, K=K_B)
+    t0 = time.perf_counter()
+    reps = 0
+    acc = 0
+    while True:
+        _, _, st, _ = oracle.select_batched(bt, seed=SEED, nthreads=cores)
+        acc += int(st[1])
+        reps += 1
+        if time.perf_counter() - t0 > 10.0 or reps >= 20:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": acc / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} pass(es) over the full batched workload (slot 0: {B_REAL} "
+                      f"realizations, {B_REAL * K_B} selections), oracle C, FP32 comparison, "
+                      f"OpenMP over selections, {dt:.1f} s"}
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    from paper_1404_0027_gb300 import build
+    build.build()
+    from paper_1404_0027_gb300 import binding as gb
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    # ---- data: N_SLOTS batches, resident in HBM --------------------------
+    slots = []
+    for i in range(N_SLOTS):
+        bt = W.batched_uneven(B=B_REAL, seed=slot_seed(rank, i), m_lo=M_LO, m_hi=M_HI, K=K_B)
+        s = {"bt": bt,
+             "alpha": torch.from_numpy(bt.alpha).to(dev),
+             "off": torch.from_numpy(bt.offsets).to(dev),
+             "oo": torch.from_numpy(bt.out_offsets).to(dev),
+             "bs": torch.empty((B_REAL, 2), dtype=torch.float64, device=dev),
+             "idx": torch.empty(int(bt.out_offsets[-1]), dtype=torch.int32, device=dev),
+             "stats": torch.zeros(3, dtype=torch.int64, device=dev),
+             "st": torch.zeros(1, dtype=torch.int32, device=dev),
+             "work": torch.zeros(max(gb.ar_select_batched_workspace_size(B_REAL), 16),
+                                 dtype=torch.uint8, device=dev)}
+        slots.append(s)
+    b_base = rank * B_REAL
+    stream = torch.cuda.Stream(dev)
+
+    def launch(s, cmp=gb.AR_CMP_F32, idx=None):
+        gb.ar_select_batched(s["alpha"], s["off"], s["oo"], SEED, 0, b_base, cmp, 1 << 20, None,
+                             s["bs"], s["idx"] if idx is None else idx, s["stats"], s["st"],
+                             s["work"], stream)
+
+    with torch.cuda.stream(stream):
+        launch(slots[0])
+    stream.synchronize()
+    bt0 = slots[0]["bt"]
+    g_idx = slots[0]["idx"].cpu().numpy()
+    # FP32 vs FP64 comparison on identical streams (paired mismatch >= paired TV)
+    idx64 = torch.empty_like(slots[0]["idx"])
+    with torch.cuda.stream(stream):
+        launch(slots[0], cmp=gb.AR_CMP_F64, idx=idx64)
+    stream.synchronize()
+    i32 = g_idx
+    i64 = idx64.cpu().numpy()
+    mismatch = float(np.mean(i32 != i64))
+    tvs = []
+    for b in range(0, B_REAL, 64):
+        lo, hi = bt0.out_offsets[b], bt0.out_offsets[b + 1]
+        Mb = int(bt0.offsets[b + 1] - bt0.offsets[b])
+        h32 = np.bincount(i32[lo:hi], minlength=Mb + 1)
+        h64 = np.bincount(i64[lo:hi], minlength=Mb + 1)
+        tvs.append(0.5 * np.abs(h32 - h64).sum() / (hi - lo))
+    paired_tv = float(np.mean(tvs))
+
+    # ---- CUDA graphs, one per slot ---------------------------------------
+    graphs = []
+    for s in slots:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            launch(s)
+        graphs.append(g)
+    for s in slots:
+        s["stats"].zero_()
+    torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        graphs[i % N_SLOTS].replay()
+    torch.cuda.synchronize()
+    for s in slots:
+        s["stats"].zero_()
+        s["st"].zero_()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    ev_all = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    sampler = ClockSampler(gpu_id_for(torch, dev))
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    with torch.cuda.stream(stream):
+        ev_all[0].record(stream)
+        for i in range(K):
+            ev[i][0].record(stream)
+            graphs[i % N_SLOTS].replay()
+            ev[i][1].record(stream)
+        ev_all[1].record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if dist:
+        dist.barrier()
+    time.sleep(0.2)
+    sampler.stop()
+    elapsed_ms = ev_all[0].elapsed_time(ev_all[1])
+    kern_ms = np.array([a.elapsed_time(b) for a, b in ev])
+    accepted = sum(int(s["stats"][1].item()) for s in slots)
+    trials = sum(int(s["stats"][0].item()) for s in slots)
+    status = 0
+    for s in slots:
+        status |= int(s["st"].item())
+    if dist:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        a = torch.tensor([accepted], dtype=torch.float64, device=dev)
+        dist.all_reduce(a)
+        accepted_all = int(a.item())
+    else:
+        accepted_all = accepted
+    value = accepted_all / (elapsed_ms * 1e-3)
+
+    # ---- roofline of the batched kernel ----------------------------------
+    peak, peak_kind, peaks = measured_peaks()
+    alg_bytes = float(np.mean([algorithmic_bytes(s["bt"]) for s in slots]))
+    kmean_s = float(kern_ms.mean()) * 1e-3
+    achieved = alg_bytes / kmean_s / 1e9
+    traffic = profiled_traffic("batched_select_cfg_batched_uneven.md")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "kernel": "k_batched<float, AR_CMP_F32>",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "kernel_ms_mean": kmean_s * 1e3, "kernel_ms_median": float(np.median(kern_ms))}
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = IMAD_PER_SM_CLK * sm_count * clk * 1e6 / PHILOX_IMAD_PER_BLOCK
+    blocks_per_launch = trials / K / 2.0
+    alu = {"bound": "alu", "achieved": blocks_per_launch / kmean_s, "peak": alu_peak,
+           "unit": "Philox4x32-10 blocks/s", "frac": blocks_per_launch / kmean_s / alu_peak,
+           "peak_from": f"{IMAD_PER_SM_CLK} IMAD/clk/SM x {sm_count} SMs x {clk:.0f} MHz / "
+                        f"{PHILOX_IMAD_PER_BLOCK} IMAD per block",
+           "trials_per_launch": trials / K}
+
+    # ---- end to end through the C ABI with host buffers ------------------
+    ke = min(K, 100)
+    s0 = slots[0]
+    h_alpha = torch.from_numpy(s0["bt"].alpha).pin_memory()
+    h_off = torch.from_numpy(s0["bt"].offsets).pin_memory()
+    h_oo = torch.from_numpy(s0["bt"].out_offsets).pin_memory()
+    h_idx = torch.empty(s0["idx"].numel(), dtype=torch.int32).pin_memory()
+    h_bs = torch.empty((B_REAL, 2), dtype=torch.float64).pin_memory()
+    h_stats = torch.empty(3, dtype=torch.int64).pin_memory()
+    d = {k: torch.empty_like(v, device=dev) for k, v in
+         (("alpha", h_alpha), ("off", h_off), ("oo", h_oo))}
+    e = {"bs": s0["bs"], "idx": s0["idx"], "stats": torch.zeros(3, dtype=torch.int64, device=dev),
+         "st": s0["st"], "work": s0["work"]}
+    h2d = h_alpha.numel() * 4 + h_off.numel() * 8 + h_oo.numel() * 8
+    d2h = h_idx.numel() * 4 + h_bs.numel() * 8 + 24
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(ke):
+            d["alpha"].copy_(h_alpha, non_blocking=True)
+            d["off"].copy_(h_off, non_blocking=True)
+            d["oo"].copy_(h_oo, non_blocking=True)
+            gb.ar_select_batched(d["alpha"], d["off"], d["oo"], SEED, 0, b_base, gb.AR_CMP_F32,
+                                 1 << 20, None, e["bs"], e["idx"], e["stats"], e["st"], e["work"],
+                                 stream)
+            h_idx.copy_(e["idx"], non_blocking=True)
+            h_bs.copy_(e["bs"], non_blocking=True)
+            h_stats.copy_(e["stats"], non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * ke * B_REAL * K_B / (e2e_ms * 1e-3)
+    e2e_ok = bool(np.array_equal(h_idx.numpy(), g_idx))
+
+    # ---- FP64-plain: one M=1024 FP64 vector, K=1000, FP64 comparison ------
+    a1 = W.plain_uniform(1024, seed=101)
+    d_a1 = torch.from_numpy(a1).to(dev)
+    p_bs = torch.empty(2, dtype=torch.float64, device=dev)
+    p_st = torch.zeros(1, dtype=torch.int32, device=dev)
+    p_idx = torch.empty(1000, dtype=torch.int32, device=dev)
+    p_stats = torch.zeros(3, dtype=torch.int64, device=dev)
+
+    def plain():
+        gb.ar_bound(d_a1, p_bs, p_st, None, stream)
+        gb.ar_select_k(d_a1, p_bs, 1000, SEED, 0, 0, gb.AR_CMP_F64, 1 << 20, p_idx, p_stats,
+                       p_st, stream)
+    with torch.cuda.stream(stream):
+        plain()
+    stream.synchronize()
+    gp = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gp, stream=stream):
+        plain()
+    for _ in range(20):
+        gp.replay()
+    torch.cuda.synchronize()
+    npl = 2000
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        f0.record(stream)
+        for _ in range(npl):
+            gp.replay()
+        f1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = f0.elapsed_time(f1) / npl
+    fp64_plain = {"value": 1000 / (plain_ms * 1e-3), "unit": UNIT, "ms_per_call": plain_ms,
+                  "workload": "one FP64 vector M=1024 alpha~U(0,1], K=1000 selections, "
+                              "ar_bound + ar_select_k, FP64 comparison, CUDA graph"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_leg()
+    clocks = sampler.summary(t_wall0, t_wall1)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": workload_config(),
+           "clocks": clocks,
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": e2e_ms / ke,
+                   "indices_match_device_run": e2e_ok},
+           "gpu_launches": K,
+           "roofline": roofline,
+           "alu_roofline": alu,
+           "cpu_baseline": cpu,
+           "fp64_plain": fp64_plain,
+           "accuracy": {"fp32_vs_fp64_index_mismatch": mismatch,
+                        "fp32_vs_fp64_paired_tv_mean": paired_tv,
+                        "status": status, "accepted_per_step": accepted / K},
+           "kernel_source_hash": kernel_source_hash()}
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

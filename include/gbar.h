@@ -95,9 +95,11 @@ int ar_last_cuda_error(void);
  *   d_status     OR-ed with BAD_ALPHA (any NaN/inf/negative; -0 is 0) or
  *                ALL_ZERO (max = 0, including M = 0).  Outputs are
  *                unspecified when BAD_ALPHA is set.
- *   d_work       scratch of ar_bound_workspace_size(M) bytes (may be NULL
- *                when that size is 0), 16-byte aligned; the call clears
- *                what it needs.
+ *   d_work       scratch of ar_bound_workspace_size(M, dtype) bytes (may be
+ *                NULL when that size is 0), 16-byte aligned.  It must be
+ *                zero-filled before its first use; every call leaves it
+ *                zero-filled again, so one call is exactly one kernel
+ *                launch.  Calls sharing a workspace must not overlap.
  * Errors: AR_ERR_ARG (M < 0, null pointers, bad dtype), AR_ERR_ALIGN,
  * AR_ERR_WORKSPACE.
  * ------------------------------------------------------------------- */
@@ -146,7 +148,9 @@ int ar_select_k(const void *d_alpha, int dtype, int64_t M, const double *d_bound
  *   plan             nullable tuning handle from ar_plan_create (NULL =
  *                    defaults).
  *   d_work           scratch of ar_select_batched_workspace_size(B) bytes,
- *                    16-byte aligned; cleared by the call.
+ *                    16-byte aligned, zero-filled before its first use;
+ *                    every call leaves it zero-filled again (one launch per
+ *                    call).  Calls sharing a workspace must not overlap.
  *   d_idx, d_stats, d_status   as in ar_select_k (status also collects
  *                    BAD_ALPHA and ALL_ZERO of any realization).
  * ------------------------------------------------------------------- */

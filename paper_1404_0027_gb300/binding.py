@@ -173,7 +173,7 @@ def bound(alpha, stream=None):
     out = torch.empty(2, dtype=torch.float64, device=dev)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     ws = ar_bound_workspace_size(alpha.numel(), _dtype_code(alpha))
-    work = torch.empty(max(ws, 16), dtype=torch.uint8, device=dev) if ws else None
+    work = torch.zeros(max(ws, 16), dtype=torch.uint8, device=dev) if ws else None
     ar_bound(alpha, out, st, work, stream)
     return out, st
 
@@ -199,7 +199,7 @@ def select_batched(alpha_cat, offsets, out_offsets, seed=1, sel_offset=0, realiz
     idx = torch.empty(int(out_offsets[-1].item()), dtype=torch.int32, device=dev)
     stats = torch.zeros(3, dtype=torch.int64, device=dev)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
-    work = torch.empty(max(ar_select_batched_workspace_size(B), 16), dtype=torch.uint8,
+    work = torch.zeros(max(ar_select_batched_workspace_size(B), 16), dtype=torch.uint8,
                        device=dev)
     ar_select_batched(alpha_cat, offsets, out_offsets, seed, sel_offset, realization_base, cmp,
                       trial_cap, plan, bs, idx, stats, st, work, stream)

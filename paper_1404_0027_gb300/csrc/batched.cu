@@ -24,9 +24,12 @@ constexpr size_t kScratch = (size_t)kWarps * 64 * sizeof(uint32_t);
 constexpr size_t kSmem = 2 * (size_t)kSlotBytes + kScratch;
 constexpr uint32_t kWaitPolls = 1u << 16;          // bounded mbarrier wait (~6 s at most)
 
+// Work queue in the caller's workspace.  It must be zero before the first
+// call; the last CTA to finish returns it to zero, so a call is one launch.
 struct BatchWork {
-  uint32_t queue;
-  uint32_t pad[3];
+  uint32_t queue;  // next realization to claim
+  uint32_t done;   // CTAs finished
+  uint32_t pad[2];
 };
 
 struct BatchParams {
@@ -288,6 +291,16 @@ __global__ void __launch_bounds__(kNT, 1) k_batched(const BatchParams p) {
   flush_counters(cnt, p.stats);
   status_acc = __reduce_or_sync(kFull, status_acc);
   if (lane == 0 && status_acc) atomicOr(p.status, status_acc);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&p.work->done, 1u) == gridDim.x - 1u) {
+      // every CTA has left the claim loop
+      p.work->queue = 0u;
+      p.work->done = 0u;
+      __threadfence();
+    }
+  }
 }
 
 template <typename TS, int CMP>
@@ -343,11 +356,6 @@ extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64
   if ((uint64_t)realization_base + (uint64_t)B > (1ull << 32)) return AR_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   BatchWork* wk = static_cast<BatchWork*>(d_work);
-  const cudaError_t e = cudaMemsetAsync(wk, 0, sizeof(BatchWork), s);
-  if (e != cudaSuccess) {
-    set_cuda_error(e);
-    return AR_ERR_CUDA;
-  }
   BatchParams p{};
   p.alpha = static_cast<const unsigned char*>(d_alpha_cat);
   p.offsets = d_offsets;

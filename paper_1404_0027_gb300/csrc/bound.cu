@@ -10,7 +10,8 @@
 // maximum on bit patterns (integer max), then accumulates the chunk in exact
 // fixed point relative to its own maximum (FP32 input) or in FP64 (FP64
 // input).  Multi-CTA launches finish in the last CTA to arrive, which
-// combines the per-CTA partials in CTA order (deterministic).
+// combines the per-CTA partials in CTA order (deterministic) and returns the
+// workspace header to zero, so a call is a single kernel launch.
 #include "device.cuh"
 #include "host.hpp"
 
@@ -68,6 +69,10 @@ __device__ void combine_partials(BoundWork* wk, int G, bool f64, double* out,
       else if (m == 0) atomicOr(status, AR_STATUS_ALL_ZERO);
       out[0] = mx;
       out[1] = s;
+      // every other CTA has published: return the workspace to zero
+      wk->counter = 0u;
+      wk->status = 0u;
+      __threadfence();
     }
   }
 }
@@ -234,11 +239,6 @@ extern "C" int ar_bound(const void* d_alpha, int dtype, int64_t M, double* d_bou
     if (work_bytes < ar_bound_workspace_size(M, dtype)) return AR_ERR_WORKSPACE;
     if (!aligned(d_work, 16)) return AR_ERR_ALIGN;
     wk = static_cast<BoundWork*>(d_work);
-    const cudaError_t e = cudaMemsetAsync(wk, 0, sizeof(BoundWork), s);
-    if (e != cudaSuccess) {
-      set_cuda_error(e);
-      return AR_ERR_CUDA;
-    }
   }
   if (dtype == AR_F32)
     k_bound_f32<<<G, kNT, 0, s>>>(static_cast<const float*>(d_alpha), M, d_bound_sum, d_status, wk);
