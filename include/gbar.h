@@ -108,6 +108,33 @@ int ar_bound(const void *d_alpha, int dtype, int64_t M, double *d_bound_sum,
              uint32_t *d_status, void *d_work, size_t work_bytes, void *stream);
 
 /* ---------------------------------------------------------------------
+ * ar_bound_noalloc -- ar_bound for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is an interface convenience.
+ * Some callers can neither call cudaMalloc nor hand over a workspace: a
+ * plug-in that a host simulator gives only its input and output buffers, a
+ * component whose host application owns every device allocation through
+ * its own pool, or a stepping loop that must not meet the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  This entry point computes exactly
+ * what ar_bound computes, with its scratch in a file-scope device array of
+ * 16 + 16 * 4096 bytes that every GPU loading the library keeps until the
+ * process exits; it calls no allocating routine.
+ *   Arguments as in ar_bound, without the workspace.
+ *   M is limited to AR_BOUND_NOALLOC_MAX_M_F32 (FP32) or
+ *   AR_BOUND_NOALLOC_MAX_M_F64 (FP64) elements; larger M returns
+ *   AR_ERR_UNSUPPORTED before anything is enqueued.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   All calls share the one array (each clears the part that must start at
+ *   zero): calls that overlap on the GPU -- on different streams, or from
+ *   different host threads -- race on it and must be serialised.
+ * ------------------------------------------------------------------- */
+#define AR_BOUND_NOALLOC_MAX_M_F32 33554432LL /* 4096 CTAs x 8192 elements */
+#define AR_BOUND_NOALLOC_MAX_M_F64 16777216LL /* 4096 CTAs x 4096 elements */
+int ar_bound_noalloc(const void *d_alpha, int dtype, int64_t M, double *d_bound_sum,
+                     uint32_t *d_status, void *stream);
+
+/* ---------------------------------------------------------------------
  * ar_select_k -- K independent selections from one propensity vector
  * (Section "A GPU acceptance-rejection algorithm": select the K next
  * reactions; the paper's K parallel realizations sharing one D in its

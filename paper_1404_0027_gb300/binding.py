@@ -50,6 +50,7 @@ SIGNATURES = {
     "ar_last_cuda_error": (_int, []),
     "ar_bound_workspace_size": (_sz, [_i64, _int]),
     "ar_bound": (_int, [_vp, _int, _i64, _vp, _vp, _vp, _sz, _vp]),
+    "ar_bound_noalloc": (_int, [_vp, _int, _i64, _vp, _vp, _vp]),
     "ar_select_k_smem_limit": (_sz, []),
     "ar_select_k": (_int, [_vp, _int, _i64, _vp, _i64, _u64, _u64, _u32, _int, _u64, _vp, _vp,
                            _vp, _vp]),
@@ -130,6 +131,15 @@ def ar_bound(alpha, bound_sum, status, work=None, stream=None):
                           _dev(bound_sum, torch.float64, "bound_sum"),
                           _dev(status, torch.int32, "status"), _dev(work, name="work"), nbytes,
                           _stream(stream)), "ar_bound")
+
+
+def ar_bound_noalloc(alpha, bound_sum, status, stream=None):
+    """ar_bound without a workspace (scratch in a static device array shared
+    by all calls; see include/gbar.h)."""
+    _check(lib().ar_bound_noalloc(_dev(alpha, name="alpha"), _dtype_code(alpha), alpha.numel(),
+                                  _dev(bound_sum, torch.float64, "bound_sum"),
+                                  _dev(status, torch.int32, "status"), _stream(stream)),
+           "ar_bound_noalloc")
 
 
 def ar_select_k_smem_limit() -> int:

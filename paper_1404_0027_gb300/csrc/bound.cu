@@ -12,6 +12,8 @@
 // input).  Multi-CTA launches finish in the last CTA to arrive, which
 // combines the per-CTA partials in CTA order (deterministic) and returns the
 // workspace header to zero, so a call is a single kernel launch.
+#include <mutex>
+
 #include "device.cuh"
 #include "host.hpp"
 
@@ -245,4 +247,67 @@ extern "C" int ar_bound(const void* d_alpha, int dtype, int64_t M, double* d_bou
   else
     k_bound_f64<<<G, kNT, 0, s>>>(static_cast<const double*>(d_alpha), M, d_bound_sum, d_status, wk);
   return check_launch();
+}
+
+// ---------------------------------------------------------------------------
+// ar_bound_noalloc: the same reduction for callers that cannot allocate
+// device memory.  Its multi-CTA scratch (the arrival counter, a status word
+// and one (max, sum) partial per CTA) lives in a file-scope device array
+// instead of a caller-provided workspace.  Every GPU that loads this library
+// holds one copy of the array until the process exits.
+// ---------------------------------------------------------------------------
+namespace gbar {
+namespace {
+constexpr int kNoAllocMaxCtas = 4096;
+constexpr size_t kNoAllocScratchBytes = sizeof(BoundWork) + (size_t)kNoAllocMaxCtas * 16;
+static_assert((int64_t)kNoAllocMaxCtas * kNT * kEptF32 == AR_BOUND_NOALLOC_MAX_M_F32, "limit");
+static_assert((int64_t)kNoAllocMaxCtas * kNT * kEptF64 == AR_BOUND_NOALLOC_MAX_M_F64, "limit");
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_scratch[64] = {};  // device address of the array, per device ordinal
+}  // namespace
+}  // namespace gbar
+
+static __device__ __align__(256) unsigned char g_bound_noalloc_scratch[gbar::kNoAllocScratchBytes];
+
+extern "C" int ar_bound_noalloc(const void* d_alpha, int dtype, int64_t M, double* d_bound_sum,
+                                uint32_t* d_status, void* stream) {
+  if (M < 0 || !valid_dtype(dtype) || !d_bound_sum || !d_status || (M > 0 && !d_alpha))
+    return AR_ERR_ARG;
+  const int64_t limit = dtype == AR_F64 ? AR_BOUND_NOALLOC_MAX_M_F64 : AR_BOUND_NOALLOC_MAX_M_F32;
+  if (M > limit) return AR_ERR_UNSUPPORTED;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return AR_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= 64) return AR_ERR_UNSUPPORTED;
+  void* scratch = nullptr;
+  {
+    // Set-up, once per device, with that device current: the host-side name
+    // of the array is only a stand-in, so ask the runtime for its address.
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_scratch[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_bound_noalloc_scratch);
+      if (e != cudaSuccess) {
+        set_cuda_error(e);
+        return AR_ERR_CUDA;
+      }
+      g_noalloc_scratch[dev] = p;
+    }
+    scratch = g_noalloc_scratch[dev];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (M > chunk_of(dtype)) {
+    // The shared array keeps the previous call's contents: clear the
+    // counter and status word the multi-CTA combine starts from.
+    e = cudaMemsetAsync(scratch, 0, sizeof(BoundWork), s);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return AR_ERR_CUDA;
+    }
+  }
+  return ar_bound(d_alpha, dtype, M, d_bound_sum, d_status, scratch, kNoAllocScratchBytes, stream);
 }
