@@ -275,13 +275,16 @@ def main():
              "stats": torch.zeros(3, dtype=torch.int64, device=dev),
              "st": torch.zeros(1, dtype=torch.int32, device=dev),
              "work": torch.zeros(max(gb.ar_select_batched_workspace_size(B_REAL), 16),
-                                 dtype=torch.uint8, device=dev)}
+                                 dtype=torch.uint8, device=dev),
+             # schedule built once per batch shape (host LPT over the CTAs)
+             "plan": gb.Plan(bt.offsets, bt.out_offsets)}
         slots.append(s)
     b_base = rank * B_REAL
     stream = torch.cuda.Stream(dev)
 
     def launch(s, cmp=gb.AR_CMP_F32, idx=None):
-        gb.ar_select_batched(s["alpha"], s["off"], s["oo"], SEED, 0, b_base, cmp, 1 << 20, None,
+        gb.ar_select_batched(s["alpha"], s["off"], s["oo"], SEED, 0, b_base, cmp, 1 << 20,
+                             s["plan"],
                              s["bs"], s["idx"] if idx is None else idx, s["stats"], s["st"],
                              s["work"], stream)
 
@@ -414,7 +417,8 @@ def main():
             d["off"].copy_(h_off, non_blocking=True)
             d["oo"].copy_(h_oo, non_blocking=True)
             gb.ar_select_batched(d["alpha"], d["off"], d["oo"], SEED, 0, b_base, gb.AR_CMP_F32,
-                                 1 << 20, None, e["bs"], e["idx"], e["stats"], e["st"], e["work"],
+                                 1 << 20, s0["plan"], e["bs"], e["idx"], e["stats"], e["st"],
+                                 e["work"],
                                  stream)
             h_idx.copy_(e["idx"], non_blocking=True)
             h_bs.copy_(e["bs"], non_blocking=True)

@@ -66,6 +66,7 @@ extern "C" {
 #define AR_STATUS_BAD_BOUND 8u  /* bound NaN, inf, < 0 (or inf in FP32)    */
 #define AR_STATUS_ABSORBED 16u  /* SSA realization reached a0 = 0          */
 #define AR_STATUS_TIMEOUT 32u   /* a bounded device wait gave up           */
+#define AR_STATUS_UNSUPPORTED 64u /* a batched realization with M_b >= 2^31 */
 
 typedef enum { AR_F32 = 0, AR_F64 = 1 } ar_dtype;
 typedef enum { AR_CMP_F32 = 0, AR_CMP_F64 = 1 } ar_cmp;
@@ -172,8 +173,11 @@ int ar_select_k(const void *d_alpha, int dtype, int64_t M, const double *d_bound
  *   d_offsets        [B+1] int64, non-decreasing, offsets[0] = 0.
  *   d_out_offsets    [B+1] int64, non-decreasing, out_offsets[0] = 0.
  *   d_bound_sum      [B][2] double out: {max, sum} per realization.
- *   plan             nullable tuning handle from ar_plan_create (NULL =
- *                    defaults).
+ *   plan             nullable handle from ar_plan_create for these offsets on
+ *                    this device (NULL: realizations are claimed dynamically
+ *                    from a work queue).  Either way the results are the same.
+ *   Realizations with M_b >= 2^31 (or decreasing offsets) are not
+ *   processed: AR_STATUS_UNSUPPORTED is raised.
  *   d_work           scratch of ar_select_batched_workspace_size(B) bytes,
  *                    16-byte aligned, zero-filled before its first use;
  *                    every call leaves it zero-filled again (one launch per
@@ -183,6 +187,26 @@ int ar_select_k(const void *d_alpha, int dtype, int64_t M, const double *d_bound
  * ------------------------------------------------------------------- */
 typedef struct ar_plan ar_plan;
 size_t ar_select_batched_workspace_size(int64_t B);
+
+/* ---------------------------------------------------------------------
+ * ar_plan_create -- tuning handle for repeated ar_select_batched calls on
+ * one batch shape (the paper's K realizations of fixed sizes, iterated
+ * over SSA steps).  Built on the host from the shape alone (no
+ * propensities): the order in which the persistent warps claim the
+ * realizations, largest estimated cost first (longest-processing-time-first
+ * list scheduling), so that the last claims of a launch are the cheapest.
+ * Results are identical with or without a plan.
+ *   h_offsets, h_out_offsets  [B+1] int64 HOST arrays, as passed (on the
+ *                device) to ar_select_batched.  A plan is valid only for
+ *                calls whose offsets have exactly these values.
+ *   *out         receives the handle.  The plan owns device memory
+ *                (4 bytes per realization) until ar_plan_destroy.
+ * Errors: AR_ERR_ARG (B <= 0, decreasing offsets, null pointers),
+ * AR_ERR_CUDA (allocation or copy failed).
+ * ------------------------------------------------------------------- */
+int ar_plan_create(const int64_t *h_offsets, const int64_t *h_out_offsets, int64_t B,
+                   ar_plan **out);
+void ar_plan_destroy(ar_plan *plan);
 int ar_select_batched(const void *d_alpha_cat, int dtype, const int64_t *d_offsets,
                       const int64_t *d_out_offsets, int64_t B, uint64_t seed,
                       uint64_t sel_offset, uint32_t realization_base, int cmp,

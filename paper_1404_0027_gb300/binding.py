@@ -32,6 +32,7 @@ AR_STATUS_TRIAL_CAP = 4
 AR_STATUS_BAD_BOUND = 8
 AR_STATUS_ABSORBED = 16
 AR_STATUS_TIMEOUT = 32
+AR_STATUS_UNSUPPORTED = 64
 
 AR_F32 = 0
 AR_F64 = 1
@@ -55,6 +56,8 @@ SIGNATURES = {
     "ar_select_k": (_int, [_vp, _int, _i64, _vp, _i64, _u64, _u64, _u32, _int, _u64, _vp, _vp,
                            _vp, _vp]),
     "ar_select_batched_workspace_size": (_sz, [_i64]),
+    "ar_plan_create": (_int, [_vp, _vp, _i64, ctypes.POINTER(ctypes.c_void_p)]),
+    "ar_plan_destroy": (None, [_vp]),
     "ar_select_batched": (_int, [_vp, _int, _vp, _vp, _i64, _u64, _u64, _u32, _int, _u64, _vp,
                                  _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
 }
@@ -160,6 +163,39 @@ def ar_select_batched_workspace_size(B: int) -> int:
     return int(lib().ar_select_batched_workspace_size(B))
 
 
+class Plan:
+    """Owner of an ar_plan handle (see ar_plan_create in include/gbar.h)."""
+
+    def __init__(self, h_offsets, h_out_offsets):
+        import numpy as np
+        self._off = np.ascontiguousarray(h_offsets, dtype=np.int64)
+        self._oo = np.ascontiguousarray(h_out_offsets, dtype=np.int64)
+        h = ctypes.c_void_p()
+        _check(lib().ar_plan_create(self._off.ctypes.data_as(ctypes.c_void_p),
+                                    self._oo.ctypes.data_as(ctypes.c_void_p),
+                                    len(self._off) - 1, ctypes.byref(h)), "ar_plan_create")
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            lib().ar_plan_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ar_plan_create(h_offsets, h_out_offsets) -> Plan:
+    return Plan(h_offsets, h_out_offsets)
+
+
+def ar_plan_destroy(plan: Plan):
+    plan.close()
+
+
 def ar_select_batched(alpha_cat, offsets, out_offsets, seed, sel_offset, realization_base, cmp,
                       trial_cap, plan, bound_sum, idx, stats, status, work, stream=None):
     B = offsets.numel() - 1
@@ -168,7 +204,7 @@ def ar_select_batched(alpha_cat, offsets, out_offsets, seed, sel_offset, realiza
         _dev(alpha_cat, name="alpha_cat"), _dtype_code(alpha_cat),
         _dev(offsets, torch.int64, "offsets"), _dev(out_offsets, torch.int64, "out_offsets"), B,
         seed, sel_offset, realization_base, cmp, trial_cap,
-        None if plan is None else ctypes.c_void_p(plan),
+        None if plan is None else ctypes.c_void_p(plan.handle if isinstance(plan, Plan) else plan),
         _dev(bound_sum, torch.float64, "bound_sum"), _dev(idx, torch.int32, "idx"),
         _dev(stats, torch.int64, "stats"), _dev(status, torch.int32, "status"),
         _dev(work, name="work"), nbytes, _stream(stream)), "ar_select_batched")

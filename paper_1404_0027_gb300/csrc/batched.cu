@@ -1,14 +1,23 @@
 // ar_select_batched: thousands of realizations with uneven M_b and K_b in one
 // persistent launch.  The paper runs K realizations as K thread blocks of M
-// threads (Section "A GPU acceptance-rejection algorithm"; 1D grid limited to
-// 65536 blocks, Section "Implementation"; several blocks per realization when
-// M exceeds a block, Discussion).  Here a grid of one CTA per SM pulls
-// realizations from a work queue; each realization's propensities are
-// streamed once from HBM into shared memory by the tensor memory accelerator
-// (cp.async.bulk completing on an mbarrier) while the previous realization
-// is being selected from (double buffering); the CTA reduces the exact
-// maximum (the threshold T) and the FP64-grade sum, then its warps run the
-// warp-level AR selection engine on the K_b selections.
+// threads (Section "A GPU acceptance-rejection algorithm"; a 1D grid limited
+// to 65536 blocks, Section "Implementation"; several blocks per realization
+// when M exceeds a block, Discussion).
+//
+// Here every warp of a persistent grid is an independent worker: it claims a
+// realization from a global queue (in the order a plan chose, largest first,
+// so the last claims are the cheap ones), streams its propensities once from
+// HBM with coalesced loads -- computing the exact maximum (the threshold T)
+// on bit patterns and an exact fixed-point sum -- and then runs the
+// warp-level selection engine of select.cuh on its K_b selections.  The
+// engine's gathers hit the realization's lines in L1 (read-only loads), so no
+// staging copy or CTA-wide barrier is needed, and warps never wait for one
+// another: a warp that finishes early claims the next realization.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
 #include "device.cuh"
 #include "host.hpp"
 #include "select.cuh"
@@ -16,23 +25,19 @@
 namespace gbar {
 namespace {
 
-constexpr int kNT = 512;
-constexpr int kWarps = kNT / 32;
-constexpr uint32_t kBufBytes = 64u * 1024u;        // one realization slot
-constexpr uint32_t kSlotBytes = kBufBytes + 16u;   // + realignment
-constexpr size_t kScratch = (size_t)kWarps * 64 * sizeof(uint32_t);
-constexpr size_t kSmem = 2 * (size_t)kSlotBytes + kScratch;
-constexpr uint32_t kWaitPolls = 1u << 16;          // bounded mbarrier wait (~6 s at most)
+constexpr int kWarps = 16;  // warps per CTA
+constexpr int kNT = kWarps * 32;
+constexpr int kCtasPerSm = 2;
+constexpr uint32_t kFxBlock = 16384;  // per-lane fixed-point block (< 2^14 terms of < 2^48)
 
-// Work queue in the caller's workspace.  It must be zero before the first
-// call; the last CTA to finish returns it to zero, so a call is one launch.
 struct BatchWork {
-  uint32_t queue;  // next realization to claim
+  uint32_t queue;  // next position of the processing order to claim
   uint32_t done;   // CTAs finished
   uint32_t pad[2];
 };
 
 struct BatchParams {
+  const uint32_t* order;  // processing order (plan), NULL: 0..B-1
   const unsigned char* alpha;
   const int64_t* offsets;
   const int64_t* out_offsets;
@@ -48,244 +53,138 @@ struct BatchParams {
   uint32_t k0, k1;
 };
 
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-// Realization descriptor held in shared memory while it is in flight.
-struct Slot {
-  int64_t a_begin;     // element offset in alpha_cat
-  uint32_t M;
-  uint32_t b;          // batch index (B = none)
-  uint32_t shift;      // byte offset of element 0 inside the slot
-  uint32_t in_smem;    // 1: staged in shared memory; 0: read from global
-};
-
-// Issues the load of realization b into slot `slot` (thread 0 only).
+// Warp reduction of one realization: exact maximum (on bit patterns),
+// validity, and the FP64-grade sum.  Every lane returns T and the sum.
 template <typename TS>
-__device__ void issue_load(const BatchParams& p, uint32_t b, Slot& sl, unsigned char* buf,
-                           uint32_t bar) {
-  sl.b = b;
-  if (b >= p.B) {
-    sl.M = 0;
-    sl.in_smem = 0;
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-    return;
-  }
-  const int64_t a0 = p.offsets[b], a1 = p.offsets[b + 1];
-  sl.a_begin = a0;
-  sl.M = (uint32_t)(a1 - a0);
-  const uintptr_t g0 = (uintptr_t)(p.alpha + a0 * (int64_t)sizeof(TS));
-  const uintptr_t g1 = g0 + (uintptr_t)sl.M * sizeof(TS);
-  sl.shift = (uint32_t)(g0 & 15u);
-  sl.in_smem = (uint64_t)sl.M * sizeof(TS) <= kBufBytes;
-  const uintptr_t lo = (g0 + 15u) & ~uintptr_t(15);
-  const uintptr_t hi = g1 & ~uintptr_t(15);
-  if (sl.in_smem && hi > lo) {
-    const uint32_t total = (uint32_t)(hi - lo);
-    mbar_expect_tx(bar, total);
-    const uint32_t dst0 = (uint32_t)__cvta_generic_to_shared(buf) + (uint32_t)(lo - (g0 & ~uintptr_t(15)));
-    for (uint32_t off = 0; off < total; off += 32768u) {
-      const uint32_t n = total - off < 32768u ? total - off : 32768u;
-      bulk_g2s(dst0 + off, (const void*)(lo + off), n, bar);
+__device__ __forceinline__ void warp_bound(const TS* __restrict__ a, uint32_t M, double& T,
+                                           double& sum, bool& bad) {
+  const uint32_t lane = threadIdx.x & 31u;
+  if constexpr (sizeof(TS) == 4) {
+    const uint32_t* u = reinterpret_cast<const uint32_t*>(a);
+    MaxF32 mx;
+    uint32_t i = lane;
+    for (; i + 96 < M; i += 128) {
+      const uint32_t x0 = __ldg(u + i), x1 = __ldg(u + i + 32), x2 = __ldg(u + i + 64),
+                     x3 = __ldg(u + i + 96);
+      mx.add(x0);
+      mx.add(x1);
+      mx.add(x2);
+      mx.add(x3);
+    }
+    for (; i < M; i += 32) mx.add(__ldg(u + i));
+    mx.smax = warp_max_i32(mx.smax);
+    mx.umax = warp_max_u32(mx.umax);
+    bad = mx.bad();
+    const uint32_t mb = mx.value_bits();
+    T = (double)__uint_as_float(mb);
+    const int e_ref = fx_eref(mb);
+    // second pass (L1 hits): exact per lane, in blocks of kFxBlock elements
+    double lane_sum = 0.0;
+    FxSum fx;
+    uint32_t in_block = 0;
+    i = lane;
+    for (; i + 96 < M; i += 128) {
+      const uint32_t x0 = __ldg(u + i), x1 = __ldg(u + i + 32), x2 = __ldg(u + i + 64),
+                     x3 = __ldg(u + i + 96);
+      fx.add(x0, e_ref);
+      fx.add(x1, e_ref);
+      fx.add(x2, e_ref);
+      fx.add(x3, e_ref);
+      if ((in_block += 4) >= kFxBlock) {
+        lane_sum = __dadd_rn(lane_sum, fx.to_double(e_ref));
+        fx = FxSum();
+        in_block = 0;
+      }
+    }
+    for (; i < M; i += 32) fx.add(__ldg(u + i), e_ref);
+    if (M < 65536u) {
+      // fewer than 2^16 terms of < 2^48 in the whole warp: exact integer sum
+      fx.warp_reduce();
+      sum = fx.to_double(e_ref);
+    } else {
+      lane_sum = __dadd_rn(lane_sum, fx.to_double(e_ref));
+      sum = warp_sum_f64(lane_sum);
     }
   } else {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+    const unsigned long long* u = reinterpret_cast<const unsigned long long*>(a);
+    MaxF64 mx;
+    double s = 0.0;
+    for (uint32_t i = lane; i < M; i += 32) {
+      const unsigned long long x = __ldg(u + i);
+      mx.add(x);
+      s = __dadd_rn(s, __longlong_as_double((long long)x));
+    }
+    mx.smax = warp_max_i64(mx.smax);
+    mx.umax = warp_max_u64(mx.umax);
+    bad = mx.bad();
+    T = __longlong_as_double((long long)mx.value_bits());
+    sum = warp_sum_f64(s);
   }
 }
 
 template <typename TS, int CMP>
-__global__ void __launch_bounds__(kNT, 1) k_batched(const BatchParams p) {
-  extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* buf[2] = {smem, smem + kSlotBytes};
-  uint32_t* scr = reinterpret_cast<uint32_t*>(smem + 2 * kSlotBytes) + (threadIdx.x >> 5) * 64;
-  __shared__ __align__(8) uint64_t bars[2];
-  __shared__ Slot slots[2];
-  __shared__ unsigned long long s_r0[kWarps], s_r1[kWarps];
-  __shared__ float s_r2[kWarps];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
-  const uint32_t bar1 = (uint32_t)__cvta_generic_to_shared(&bars[1]);
-
-  if (threadIdx.x == 0) {
-    mbar_init(bar0, 1);
-    mbar_init(bar1, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    const uint32_t b = atomicAdd(&p.work->queue, 1u);
-    issue_load<TS>(p, b, slots[0], buf[0], bar0);
-  }
-  __syncthreads();
-
+__global__ void __launch_bounds__(kNT, kCtasPerSm) k_batched(const BatchParams p) {
+  __shared__ uint32_t s_scr[kWarps * 64];
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t* scr = s_scr + (threadIdx.x >> 5) * 64;
   SelCounters cnt;
   uint32_t status_acc = 0;
-  for (uint32_t it = 0;; ++it) {
-    const uint32_t cur = it & 1u;
-    const Slot sl = slots[cur];
-    if (sl.b >= p.B) break;
-    if (threadIdx.x == 0) {
-      const uint32_t nb = atomicAdd(&p.work->queue, 1u);
-      issue_load<TS>(p, nb, slots[cur ^ 1u], buf[cur ^ 1u], cur ? bar0 : bar1);
-    }
-    const bool landed = mbar_wait(&bars[cur], (it >> 1) & 1u, kWaitPolls);
-    if (__syncthreads_or(!landed)) {
-      if (threadIdx.x == 0) atomicOr(p.status, AR_STATUS_TIMEOUT);
-      break;
-    }
-    const TS* g_alpha = reinterpret_cast<const TS*>(p.alpha) + sl.a_begin;
-    const TS* a = sl.in_smem ? reinterpret_cast<const TS*>(buf[cur] + sl.shift) : g_alpha;
-    const uint32_t M = sl.M;
-    if (sl.in_smem) {
-      // Elements outside the 16-byte aligned range moved by the bulk copy:
-      // [0, head) and [tail, M) (all of them when no aligned block exists).
-      const int64_t g0 = (int64_t)(uintptr_t)g_alpha;
-      const int64_t g1 = g0 + (int64_t)M * (int64_t)sizeof(TS);
-      const int64_t lo = (g0 + 15) & ~int64_t(15), hi = g1 & ~int64_t(15);
-      int64_t head = (lo - g0) / (int64_t)sizeof(TS);
-      int64_t tail = (hi - g0) / (int64_t)sizeof(TS);
-      if (hi <= lo) head = tail = M;  // no bulk copy was issued: load everything
-      if (head > M) head = M;
-      if (tail < head) tail = head;
-      TS* w = reinterpret_cast<TS*>(buf[cur] + sl.shift);
-      for (int64_t i = threadIdx.x; i < head; i += kNT) w[i] = g_alpha[i];
-      for (int64_t i = tail + threadIdx.x; i < M; i += kNT) w[i] = g_alpha[i];
-    }
-    __syncthreads();
-
-    // ---- bound: exact maximum and FP64-grade sum ------------------------
-    double T;
-    bool bad;
-    if constexpr (sizeof(TS) == 4) {
-      MaxF32 mx;
-      for (uint32_t i = threadIdx.x; i < M; i += kNT) mx.add(__float_as_uint(a[i]));
-      mx.smax = warp_max_i32(mx.smax);
-      mx.umax = warp_max_u32(mx.umax);
-      if (lane == 0) {
-        s_r0[warp] = (unsigned long long)(uint32_t)mx.smax;
-        s_r1[warp] = mx.umax;
-      }
-      __syncthreads();
-      int32_t sm = INT32_MIN;
-      uint32_t um = 0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) {
-        sm = max(sm, (int32_t)(uint32_t)s_r0[w]);
-        um = max(um, (uint32_t)s_r1[w]);
-      }
-      mx.smax = sm;
-      mx.umax = um;
-      bad = mx.bad();
-      const uint32_t mbits = mx.value_bits();
-      T = (double)__uint_as_float(mbits);
-      const int e_ref = fx_eref(mbits);
-      FxSum fx;
-      for (uint32_t i = threadIdx.x; i < M; i += kNT) fx.add(__float_as_uint(a[i]), e_ref);
-      fx.warp_reduce();
-      __syncthreads();  // s_r* reuse
-      if (lane == 0) {
-        s_r0[warp] = fx.a1;
-        s_r1[warp] = fx.a2;
-        s_r2[warp] = fx.a3;
-      }
-      __syncthreads();
-      if (warp == 0) {
-        FxSum f;
-        if (lane < kWarps) {
-          f.a1 = s_r0[lane];
-          f.a2 = s_r1[lane];
-          f.a3 = s_r2[lane];
-        }
-        f.warp_reduce();
-        if (lane == 0) {
-          double* o = p.bound_sum + 2 * (size_t)sl.b;
-          o[0] = T;
-          o[1] = f.to_double(e_ref);
-        }
-      }
-    } else {
-      MaxF64 mx;
-      double sum = 0.0;
-      for (uint32_t i = threadIdx.x; i < M; i += kNT) {
-        const double x = a[i];
-        mx.add((unsigned long long)__double_as_longlong(x));
-        sum = __dadd_rn(sum, x);
-      }
-      mx.smax = warp_max_i64(mx.smax);
-      mx.umax = warp_max_u64(mx.umax);
-      sum = warp_sum_f64(sum);
-      if (lane == 0) {
-        s_r0[warp] = (unsigned long long)mx.smax;
-        s_r1[warp] = mx.umax;
-      }
-      __shared__ double s_sum[kWarps];
-      if (lane == 0) s_sum[warp] = sum;
-      __syncthreads();
-      long long sm = INT64_MIN;
-      unsigned long long um = 0;
-      double tot = 0.0;
-#pragma unroll
-      for (int w = 0; w < kWarps; ++w) {
-        sm = max(sm, (long long)s_r0[w]);
-        um = max(um, s_r1[w]);
-      }
-      if (warp == 0) {
-        tot = lane < kWarps ? s_sum[lane] : 0.0;
-        tot = warp_sum_f64(tot);
-      }
-      mx.smax = sm;
-      mx.umax = um;
-      bad = mx.bad();
-      T = __longlong_as_double((long long)mx.value_bits());
-      if (threadIdx.x == 0) {
-        double* o = p.bound_sum + 2 * (size_t)sl.b;
-        o[0] = T;
-        o[1] = tot;
-      }
-    }
-    uint32_t st = 0;
-    if (bad) st = AR_STATUS_BAD_ALPHA;
-    else if (T == 0.0) st = AR_STATUS_ALL_ZERO;
-    const float Tf = __double2float_rn(T);
-    if (CMP == AR_CMP_F32 && !st && isinf(Tf)) st = AR_STATUS_BAD_BOUND;
-
-    // ---- selections ------------------------------------------------------
-    const int64_t o0 = p.out_offsets[sl.b];
-    const uint32_t Kb = (uint32_t)(p.out_offsets[sl.b + 1] - o0);
+  for (;;) {
+    uint32_t i = 0;
+    if (lane == 0) i = atomicAdd(&p.work->queue, 1u);
+    i = __shfl_sync(kFull, i, 0);
+    if (i >= p.B) break;
+    const uint32_t b = p.order ? __ldg(p.order + i) : i;
+    int64_t v = 0;
+    if (lane < 2) v = __ldg(p.offsets + b + lane);
+    else if (lane < 4) v = __ldg(p.out_offsets + b + lane - 2);
+    const int64_t a0 = __shfl_sync(kFull, v, 0), a1 = __shfl_sync(kFull, v, 1);
+    const int64_t o0 = __shfl_sync(kFull, v, 2), o1 = __shfl_sync(kFull, v, 3);
+    const uint32_t K = o1 > o0 ? (uint32_t)(o1 - o0) : 0u;
     int32_t* idx = p.idx + o0;
-    const uint32_t per = (Kb + kWarps - 1) / kWarps;
-    const uint32_t q = min(Kb, per * (uint32_t)warp);
-    const uint32_t q_end = min(Kb, q + per);
+    uint32_t st = 0;
+    uint32_t M = 0;
+    if (a1 < a0 || a1 - a0 >= (1ll << 31)) {
+      st = AR_STATUS_UNSUPPORTED;
+      M = a1 < a0 ? 0u : 0x7fffffffu;
+    } else {
+      M = (uint32_t)(a1 - a0);
+    }
+    const TS* a = reinterpret_cast<const TS*>(p.alpha) + a0;
+    double T = 0.0, sum = 0.0;
+    if (!st) {
+      bool bad = false;
+      warp_bound<TS>(a, M, T, sum, bad);
+      if (bad) st = AR_STATUS_BAD_ALPHA;
+      else if (T == 0.0) st = AR_STATUS_ALL_ZERO;
+      else if (CMP == AR_CMP_F32 && isinf(__double2float_rn(T))) st = AR_STATUS_BAD_BOUND;
+    }
+    if (lane == 0) {
+      double* o = p.bound_sum + 2 * (size_t)b;
+      o[0] = T;
+      o[1] = sum;
+    }
     if (st) {
       status_acc |= st;
-      warp_fill(q, q_end, (int32_t)M, idx);
-    } else if (q < q_end) {
-      const uint32_t bid = p.b_base + sl.b;
-      if constexpr (CMP == AR_CMP_F32) {
-        auto acc = [&](uint32_t j, uint32_t w) -> bool {
-          float x;
-          if constexpr (sizeof(TS) == 4) x = a[j];
-          else x = __double2float_rn(a[j]);
-          return accept_f32(w, Tf, x);
-        };
-        warp_select(q, q_end, p.sel_base, M, bid, p.k0, p.k1, p.cap, acc, idx, scr, cnt);
-      } else {
-        auto acc = [&](uint32_t j, uint32_t w) -> bool { return accept_f64(w, T, (double)a[j]); };
-        warp_select(q, q_end, p.sel_base, M, bid, p.k0, p.k1, p.cap, acc, idx, scr, cnt);
-      }
+      warp_fill(0, K, (int32_t)M, idx);
+      continue;
     }
-    __syncthreads();  // slot `cur` is free for the load issued next iteration
+    const uint32_t bid = p.b_base + b;
+    if constexpr (CMP == AR_CMP_F32) {
+      const float Tf = __double2float_rn(T);
+      auto acc = [&](uint32_t j, uint32_t w) -> bool {
+        float x;
+        if constexpr (sizeof(TS) == 4) x = __ldg(a + j);
+        else x = __double2float_rn(__ldg(a + j));
+        return accept_f32(w, Tf, x);
+      };
+      warp_select(0u, K, p.sel_base, M, bid, p.k0, p.k1, p.cap, acc, idx, scr, cnt);
+    } else {
+      auto acc = [&](uint32_t j, uint32_t w) -> bool {
+        return accept_f64(w, T, (double)__ldg(a + j));
+      };
+      warp_select(0u, K, p.sel_base, M, bid, p.k0, p.k1, p.cap, acc, idx, scr, cnt);
+    }
   }
   if (cnt.capped) status_acc |= AR_STATUS_TRIAL_CAP;
   flush_counters(cnt, p.stats);
@@ -295,7 +194,7 @@ __global__ void __launch_bounds__(kNT, 1) k_batched(const BatchParams p) {
   if (threadIdx.x == 0) {
     __threadfence();
     if (atomicAdd(&p.work->done, 1u) == gridDim.x - 1u) {
-      // every CTA has left the claim loop
+      // every CTA has left the claim loop: return the queue to zero
       p.work->queue = 0u;
       p.work->done = 0u;
       __threadfence();
@@ -306,22 +205,15 @@ __global__ void __launch_bounds__(kNT, 1) k_batched(const BatchParams p) {
 template <typename TS, int CMP>
 int launch(const BatchParams& p, cudaStream_t s) {
   auto kern = k_batched<TS, CMP>;
-  static bool configured[64] = {false};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 64 && !configured[dev]) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-    if (e != cudaSuccess) {
-      set_cuda_error(e);
-      return AR_ERR_CUDA;
-    }
-    configured[dev] = true;
-  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, 0);
+  if (per_sm < 1) per_sm = 1;
   const DeviceInfo& d = device_info();
-  const unsigned sms = (unsigned)(d.sm_count > 0 ? d.sm_count : 1);
-  const unsigned grid = sms < p.B ? sms : p.B;
-  kern<<<grid, kNT, kSmem, s>>>(p);
+  const uint64_t sms = (uint64_t)(d.sm_count > 0 ? d.sm_count : 1);
+  // no more CTAs than needed to give every realization its own warp
+  const uint64_t need = ((uint64_t)p.B + kWarps - 1) / kWarps;
+  const unsigned grid = (unsigned)std::min<uint64_t>(sms * (uint64_t)per_sm, need);
+  kern<<<grid, kNT, 0, s>>>(p);
   return check_launch();
 }
 
@@ -329,6 +221,60 @@ int launch(const BatchParams& p, cudaStream_t s) {
 }  // namespace gbar
 
 using namespace gbar;
+
+// The processing order of a batch: realizations sorted by an estimate of
+// their cost, largest first, so that the work still unclaimed near the end
+// of a launch is the cheapest (longest-processing-time-first list
+// scheduling over the persistent warps).
+struct ar_plan {
+  int device;
+  int64_t B;
+  uint32_t* d_order;
+};
+
+extern "C" int ar_plan_create(const int64_t* h_offsets, const int64_t* h_out_offsets, int64_t B,
+                              ar_plan** out) {
+  if (!out || B <= 0 || B >= (1ll << 31) || !h_offsets || !h_out_offsets) return AR_ERR_ARG;
+  *out = nullptr;
+  // cost model: one streaming pass over M_b plus K_b selections whose trial
+  // count grows like log M_b for spread-out propensities
+  std::vector<double> cost(B);
+  for (int64_t b = 0; b < B; ++b) {
+    const int64_t M = h_offsets[b + 1] - h_offsets[b];
+    const int64_t K = h_out_offsets[b + 1] - h_out_offsets[b];
+    if (M < 0 || K < 0) return AR_ERR_ARG;
+    cost[b] = 0.4 * (double)M + 1.7 * (double)K * (0.6 + std::log((double)std::max<int64_t>(M, 2)));
+  }
+  std::vector<uint32_t> order(B);
+  std::iota(order.begin(), order.end(), 0u);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](uint32_t x, uint32_t y) { return cost[x] > cost[y]; });
+  auto* p = new ar_plan();
+  p->device = device_info().device;
+  p->B = B;
+  p->d_order = nullptr;
+  cudaError_t e = cudaMalloc(&p->d_order, sizeof(uint32_t) * (size_t)B);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_order, order.data(), sizeof(uint32_t) * (size_t)B, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    cudaFree(p->d_order);
+    delete p;
+    return AR_ERR_CUDA;
+  }
+  *out = p;
+  return AR_OK;
+}
+
+extern "C" void ar_plan_destroy(ar_plan* plan) {
+  if (!plan) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != plan->device) cudaSetDevice(plan->device);
+  cudaFree(plan->d_order);
+  if (cur != plan->device) cudaSetDevice(cur);
+  delete plan;
+}
 
 extern "C" size_t ar_select_batched_workspace_size(int64_t B) {
   (void)B;
@@ -341,7 +287,6 @@ extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64
                                  uint64_t trial_cap, const ar_plan* plan, double* d_bound_sum,
                                  int32_t* d_idx, ar_stats* d_stats, uint32_t* d_status,
                                  void* d_work, size_t work_bytes, void* stream) {
-  (void)plan;
   if (!valid_dtype(dtype) || !valid_cmp(cmp) || B < 0 || B >= (1ll << 31)) return AR_ERR_ARG;
   if (trial_cap < 1 || trial_cap > (1ull << 32)) return AR_ERR_ARG;
   if (B == 0) return AR_OK;
@@ -354,9 +299,15 @@ extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64
   if (!d_work || work_bytes < ar_select_batched_workspace_size(B)) return AR_ERR_WORKSPACE;
   if (!aligned(d_work, 16)) return AR_ERR_ALIGN;
   if ((uint64_t)realization_base + (uint64_t)B > (1ull << 32)) return AR_ERR_ARG;
+  if (sel_offset >= (1ull << 32)) return AR_ERR_ARG;
+  if (plan) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (plan->B != B || plan->device != dev) return AR_ERR_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  BatchWork* wk = static_cast<BatchWork*>(d_work);
   BatchParams p{};
+  p.order = plan ? plan->d_order : nullptr;
   p.alpha = static_cast<const unsigned char*>(d_alpha_cat);
   p.offsets = d_offsets;
   p.out_offsets = d_out_offsets;
@@ -364,7 +315,7 @@ extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64
   p.idx = d_idx;
   p.stats = d_stats;
   p.status = d_status;
-  p.work = wk;
+  p.work = static_cast<BatchWork*>(d_work);
   p.cap = trial_cap;
   p.B = (uint32_t)B;
   p.sel_base = (uint32_t)sel_offset;

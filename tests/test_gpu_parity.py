@@ -148,10 +148,11 @@ def test_select_degenerate(gb, orc):
 
 
 # -------------------------------------------------------- ar_select_batched
-def _check_batched(gb, orc, bt, cmp=0, seed=1, sel_offset=0, realization_base=0):
+def _check_batched(gb, orc, bt, cmp=0, seed=1, sel_offset=0, realization_base=0, plan=False):
+    pl = gb.Plan(bt.offsets, bt.out_offsets) if plan else None
     bs, idx, stats, st = gb.select_batched(_t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets),
                                            seed=seed, sel_offset=sel_offset,
-                                           realization_base=realization_base, cmp=cmp)
+                                           realization_base=realization_base, cmp=cmp, plan=pl)
     obs, oidx, ostats, ost = orc.select_batched(bt, seed=seed, sel_offset=sel_offset,
                                                 realization_base=realization_base, cmp=cmp,
                                                 nthreads=8)
@@ -167,23 +168,61 @@ def _check_batched(gb, orc, bt, cmp=0, seed=1, sel_offset=0, realization_base=0)
     assert int(st.item()) == ost
 
 
+@pytest.mark.parametrize("plan", [False, True])
 @pytest.mark.parametrize("cmp", [0, 1])
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
-def test_batched_ragged(gb, orc, cmp, dtype):
+def test_batched_ragged(gb, orc, cmp, dtype, plan):
     vecs = [W.skewed(m, seed=m).astype(dtype) for m in (1, 2, 3, 5, 7, 64, 1000, 4099, 16384,
                                                           20_000, 9, 1)]
     vecs.append(np.zeros(33, dtype=dtype))
     ks = [5, 0, 17, 1, 256, 300, 256, 1000, 64, 77, 3, 2, 9]
     _check_batched(gb, orc, W.batch_from_vectors(vecs, ks), cmp=cmp, seed=7, sel_offset=11,
-                   realization_base=100)
+                   realization_base=100, plan=plan)
 
 
+@pytest.mark.parametrize("plan", [False, True])
 @pytest.mark.parametrize("cmp", [0, 1])
-def test_batched_uneven_small(gb, orc, cmp):
-    _check_batched(gb, orc, W.batched_uneven(B=300, seed=301, K=256), cmp=cmp)
+def test_batched_uneven_small(gb, orc, cmp, plan):
+    _check_batched(gb, orc, W.batched_uneven(B=300, seed=301, K=256), cmp=cmp, plan=plan)
 
 
-def test_batched_uneven_full(gb, orc):
+@pytest.mark.parametrize("plan", [False, True])
+@pytest.mark.parametrize("seed", [300, 301, 305])
+def test_batched_uneven_full(gb, orc, seed, plan):
     """The full batched workload: 4096 realizations, M_b log-uniform in
-    [64, 16384], K_b = 256, FP32 comparison."""
-    _check_batched(gb, orc, W.batched_uneven())
+    [64, 16384], K_b = 256, FP32 comparison (the benchmark's launch)."""
+    _check_batched(gb, orc, W.batched_uneven(seed=seed), plan=plan)
+
+
+def test_batched_repeated_launches_reuse_workspace(gb, orc):
+    """Back-to-back launches on one workspace (the benchmark's pattern, also
+    under graph replay) give identical results: the queue returns to zero."""
+    import torch
+    bt = W.batched_uneven(B=1000, seed=302, K=64)
+    a, off, oo = _t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets)
+    work = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    bs = torch.empty((bt.B, 2), dtype=torch.float64, device="cuda")
+    idx = torch.empty(int(bt.out_offsets[-1]), dtype=torch.int32, device="cuda")
+    stats = torch.zeros(3, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _, oidx, _, _ = orc.select_batched(bt, nthreads=8)
+    s = torch.cuda.Stream()
+    for plan in (None, gb.Plan(bt.offsets, bt.out_offsets)):
+        with torch.cuda.stream(s):
+            for _ in range(5):
+                idx.fill_(-1)
+                gb.ar_select_batched(a, off, oo, 1, 0, 0, 0, 1 << 20, plan, bs, idx, stats, st,
+                                     work, s)
+                s.synchronize()
+                assert np.array_equal(idx.cpu().numpy(), oidx)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                gb.ar_select_batched(a, off, oo, 1, 0, 0, 0, 1 << 20, plan, bs, idx, stats, st,
+                                     work, s)
+            for _ in range(3):
+                idx.fill_(-1)
+                g.replay()
+                s.synchronize()
+                assert np.array_equal(idx.cpu().numpy(), oidx)
+        assert work.cpu().numpy().tolist() == [0] * 16
+    assert int(st.item()) == 0
