@@ -214,6 +214,58 @@ int ar_select_batched(const void *d_alpha_cat, int dtype, const int64_t *d_offse
                       int32_t *d_idx, ar_stats *d_stats, uint32_t *d_status,
                       void *d_work, size_t work_bytes, void *stream);
 
+/* ---------------------------------------------------------------------
+ * SSA step (Section "The Stochastic Simulation Algorithm": select j, draw
+ * tau = ln(1/u)/a_0, X += v_j, t += tau; the selection is the AR trial
+ * above with T = max_j a_j and selection id = the realization's step
+ * number).  Mass-action propensities a_r = c_r * h_r(X) with one FP64
+ * rounding of the exact integer count h_r:
+ *   type 0 (source)  h = 1
+ *   type 1 (A)       h = x_A (0 if x_A <= 0)
+ *   type 2 (A + B)   h = x_A x_B (0 if either <= 0)
+ *   type 3 (2A)      h = x_A (x_A - 1) / 2 (0 if x_A < 2)
+ * After reaction j only the propensities of reactions that read a species
+ * j changes are recomputed (dependency graph, Gibson & Bruck, cited in the
+ * Introduction); a_0 is kept as an exact fixed-point sum.
+ *
+ * ssa_net_create -- uploads a network: h_rtype[M], h_reactants[M][2]
+ *   (species A, B; -1 where unused), h_rate[M] (finite, >= 0), the net
+ *   state change as CSR h_nu_ptr[M+1], h_nu_species[nnz], h_nu_delta[nnz]
+ *   (each species at most once per reaction).  Builds the dependency graph.
+ *   The handle owns device memory until ssa_net_destroy.  AR_ERR_ARG on an
+ *   invalid network, AR_ERR_CUDA on allocation failure.
+ * ------------------------------------------------------------------- */
+typedef struct ssa_net ssa_net;
+int ssa_net_create(int32_t N, int32_t M, const int32_t *h_rtype, const int32_t *h_reactants,
+                   const double *h_rate, const int32_t *h_nu_ptr, const int32_t *h_nu_species,
+                   const int32_t *h_nu_delta, ssa_net **out);
+void ssa_net_destroy(ssa_net *net);
+
+/* ---------------------------------------------------------------------
+ * ssa_step_batched -- advances B realizations by up to nsteps steps each.
+ *   d_X       [B][N] int32 molecule counts (in/out).
+ *   d_a       [B][M] double scratch/out: the propensities of the final state
+ *             (recomputed from d_X at the start of every call).
+ *   d_t       [B] double time (in/out); d_step [B] uint64 step counters
+ *             (in/out; the selection id of a step is its counter, so a run
+ *             split over several calls draws the same random numbers as one
+ *             call).
+ *   seed, realization_base  random stream; realization b uses id
+ *             realization_base + b; tau uses counter (0, step, id, 1).
+ *   cmp, trial_cap  as in ar_select_k.
+ *   d_last    nullable [B] int32: the last reaction fired.
+ *   d_status  [B] uint32 (in/out): ABSORBED (a_0 = 0: the realization
+ *             stops), TRIAL_CAP (stops), UNSUPPORTED (the fixed-point a_0
+ *             left its range: propensities grew 2^40-fold within the call).
+ *             Realizations whose status already holds ABSORBED, TRIAL_CAP,
+ *             BAD_ALPHA or UNSUPPORTED are not advanced.
+ *   d_trials  nullable [B] uint64: trials consumed are added.
+ * ------------------------------------------------------------------- */
+int ssa_step_batched(const ssa_net *net, int64_t B, int32_t *d_X, double *d_a, double *d_t,
+                     uint64_t *d_step, int64_t nsteps, uint64_t seed, uint32_t realization_base,
+                     int cmp, uint64_t trial_cap, int32_t *d_last, uint32_t *d_status,
+                     uint64_t *d_trials, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,11 @@ SIGNATURES = {
                            _vp, _vp]),
     "ar_select_batched_workspace_size": (_sz, [_i64]),
     "ar_plan_create": (_int, [_vp, _vp, _i64, ctypes.POINTER(ctypes.c_void_p)]),
+    "ssa_net_create": (_int, [ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp,
+                              ctypes.POINTER(ctypes.c_void_p)]),
+    "ssa_net_destroy": (None, [_vp]),
+    "ssa_step_batched": (_int, [_vp, _i64, _vp, _vp, _vp, _vp, _i64, _u64, _u32, _int, _u64,
+                                _vp, _vp, _vp, _vp]),
     "ar_plan_destroy": (None, [_vp]),
     "ar_select_batched": (_int, [_vp, _int, _vp, _vp, _i64, _u64, _u64, _u32, _int, _u64, _vp,
                                  _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
@@ -250,3 +255,80 @@ def select_batched(alpha_cat, offsets, out_offsets, seed=1, sel_offset=0, realiz
     ar_select_batched(alpha_cat, offsets, out_offsets, seed, sel_offset, realization_base, cmp,
                       trial_cap, plan, bs, idx, stats, st, work, stream)
     return bs, idx, stats, st
+
+
+# --------------------------------------------------------------------------
+# SSA
+# --------------------------------------------------------------------------
+class SsaNet:
+    """Owner of an ssa_net handle built from a workloads.Network."""
+
+    def __init__(self, net):
+        import numpy as np
+        self._arrs = [np.ascontiguousarray(x, dtype=dt) for x, dt in (
+            (net.rtype, np.int32), (net.reactants, np.int32), (net.rate, np.float64),
+            (net.nu_ptr, np.int32), (net.nu_species, np.int32), (net.nu_delta, np.int32))]
+        h = ctypes.c_void_p()
+        _check(lib().ssa_net_create(net.n_species, net.M,
+                                    *[x.ctypes.data_as(ctypes.c_void_p) for x in self._arrs],
+                                    ctypes.byref(h)), "ssa_net_create")
+        self.handle = h.value
+        self.N, self.M = net.n_species, net.M
+
+    def close(self):
+        if self.handle:
+            lib().ssa_net_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ssa_net_create(net) -> SsaNet:
+    return SsaNet(net)
+
+
+def ssa_net_destroy(net: SsaNet):
+    net.close()
+
+
+def ssa_step_batched(net, X, a, t, step, nsteps, seed, realization_base, cmp, trial_cap, last,
+                     status, trials, stream=None):
+    """X int32 [B,N], a f64 [B,M], t f64 [B], step int64 [B], last int32 [B] or None,
+    status int32 [B], trials int64 [B] or None (all CUDA tensors)."""
+    B = X.shape[0]
+    _check(lib().ssa_step_batched(ctypes.c_void_p(net.handle), B, _dev(X, torch.int32, "X"),
+                                  _dev(a, torch.float64, "a"), _dev(t, torch.float64, "t"),
+                                  _dev(step, torch.int64, "step"), nsteps, seed, realization_base,
+                                  cmp, trial_cap, _dev(last, torch.int32, "last"),
+                                  _dev(status, torch.int32, "status"),
+                                  _dev(trials, torch.int64, "trials"), _stream(stream)),
+           "ssa_step_batched")
+
+
+def ssa_run(net, X0, nsteps, seed=1, realization_base=0, cmp=AR_CMP_F32, trial_cap=1 << 20,
+            t=None, step=None, status=None, stream=None):
+    """Convenience: copies X0 (numpy or tensor) to the device and runs nsteps.
+    -> dict of CUDA tensors X, a, t, step, last, status, trials."""
+    import numpy as np
+    dev = torch.device("cuda")
+    Xd = torch.as_tensor(np.ascontiguousarray(X0, dtype=np.int32)).to(dev).contiguous()
+    B = Xd.shape[0]
+    out = dict(
+        X=Xd,
+        a=torch.zeros((B, net.M), dtype=torch.float64, device=dev),
+        t=(torch.zeros(B, dtype=torch.float64, device=dev) if t is None
+           else torch.as_tensor(t, dtype=torch.float64).to(dev).contiguous()),
+        step=(torch.zeros(B, dtype=torch.int64, device=dev) if step is None
+              else torch.as_tensor(np.asarray(step).astype(np.int64)).to(dev).contiguous()),
+        last=-torch.ones(B, dtype=torch.int32, device=dev),
+        status=(torch.zeros(B, dtype=torch.int32, device=dev) if status is None
+                else torch.as_tensor(np.asarray(status).astype(np.int32)).to(dev).contiguous()),
+        trials=torch.zeros(B, dtype=torch.int64, device=dev))
+    ssa_step_batched(net, out["X"], out["a"], out["t"], out["step"], nsteps, seed,
+                     realization_base, cmp, trial_cap, out["last"], out["status"],
+                     out["trials"], stream)
+    return out
