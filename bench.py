@@ -241,6 +241,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ssa", action="store_true")
+    ap.add_argument("--ssa-steps", type=int, default=10_000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -467,6 +469,60 @@ def main():
                   "workload": "one FP64 vector M=1024 alpha~U(0,1], K=1000 selections, "
                               "ar_bound + ar_select_k, FP64 comparison, CUDA graph"}
 
+    # ---- full batched SSA: 10^4 realizations x 10^4 steps ------------------
+    ssa = None
+    if not args.no_ssa:
+        net = W.random_network(N=641, M=1029, seed=500)
+        gnet = gb.SsaNet(net)
+        B_ssa, n_ssa = 10_000, args.ssa_steps
+        X0 = torch.from_numpy(W.initial_counts(641, B_ssa, seed=501 + rank)).to(dev)
+        sx = {"X": torch.empty_like(X0), "a": torch.empty((B_ssa, 1029), dtype=torch.float64,
+                                                          device=dev),
+              "t": torch.zeros(B_ssa, dtype=torch.float64, device=dev),
+              "step": torch.zeros(B_ssa, dtype=torch.int64, device=dev),
+              "last": torch.zeros(B_ssa, dtype=torch.int32, device=dev),
+              "status": torch.zeros(B_ssa, dtype=torch.int32, device=dev),
+              "trials": torch.zeros(B_ssa, dtype=torch.int64, device=dev)}
+
+        def ssa_run():
+            sx["X"].copy_(X0)
+            sx["t"].zero_()
+            sx["step"].zero_()
+            sx["status"].zero_()
+            sx["trials"].zero_()
+            gb.ssa_step_batched(gnet, sx["X"], sx["a"], sx["t"], sx["step"], n_ssa, SEED,
+                                rank * B_ssa, gb.AR_CMP_F32, 1 << 20, sx["last"], sx["status"],
+                                sx["trials"], stream)
+        with torch.cuda.stream(stream):
+            ssa_run()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(3):
+            s0e, s1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                sx["X"].copy_(X0)
+                sx["t"].zero_()
+                sx["step"].zero_()
+                sx["status"].zero_()
+                sx["trials"].zero_()
+                s0e.record(stream)
+                gb.ssa_step_batched(gnet, sx["X"], sx["a"], sx["t"], sx["step"], n_ssa, SEED,
+                                    rank * B_ssa, gb.AR_CMP_F32, 1 << 20, sx["last"],
+                                    sx["status"], sx["trials"], stream)
+                s1e.record(stream)
+            torch.cuda.synchronize()
+            times.append(s0e.elapsed_time(s1e))
+        steps_done = int(sx["step"].sum().item())
+        ms = float(np.median(times))
+        ssa = {"value": steps_done / (ms * 1e-3), "unit": "SSA steps/s",
+               "selections_per_s": steps_done / (ms * 1e-3), "kernel_ms": ms,
+               "trials_per_step": float(sx["trials"].sum().item()) / max(steps_done, 1),
+               "status_or": int(np.bitwise_or.reduce(sx["status"].cpu().numpy())),
+               "workload": f"{B_ssa} realizations of a random mass-action network "
+                           f"(641 species, 1029 uni/bi/dimer reactions, seed 500), "
+                           f"{n_ssa} steps each, FP32 comparison, FP64 propensities"}
+        gnet.close()
+
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -488,6 +544,7 @@ def main():
            "alu_roofline": alu,
            "cpu_baseline": cpu,
            "fp64_plain": fp64_plain,
+           "ssa": ssa,
            "accuracy": {"fp32_vs_fp64_index_mismatch": mismatch,
                         "fp32_vs_fp64_paired_tv_mean": paired_tv,
                         "status": status, "accepted_per_step": accepted / K},
