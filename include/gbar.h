@@ -161,8 +161,9 @@ int ar_select_k(const void *d_alpha, int dtype, int64_t M, const double *d_bound
                 uint32_t *d_status, void *stream);
 
 /* ---------------------------------------------------------------------
- * ar_select_batched -- many realizations with uneven M_b and K_b in one
- * persistent launch (Section "A GPU acceptance-rejection algorithm": K
+ * ar_select_batched -- many realizations with uneven M_b and K_b in two
+ * persistent launches enqueued on the stream, a chunked reduction and the
+ * selections (Section "A GPU acceptance-rejection algorithm": K
  * realizations as K blocks; the text's extension to M beyond one block).
  * Realization b owns alpha_cat[offsets[b] .. offsets[b+1]) and writes
  * K_b = out_offsets[b+1] - out_offsets[b] indices at d_idx[out_offsets[b]].
@@ -172,16 +173,24 @@ int ar_select_k(const void *d_alpha, int dtype, int64_t M, const double *d_bound
  *   d_alpha_cat      FP32 or FP64 (dtype).
  *   d_offsets        [B+1] int64, non-decreasing, offsets[0] = 0.
  *   d_out_offsets    [B+1] int64, non-decreasing, out_offsets[0] = 0.
- *   d_bound_sum      [B][2] double out: {max, sum} per realization.
+ *   d_bound_sum      [B][2] double out: {max, sum} per realization.  FP32
+ *                    data: sum is the exact total rounded once to FP64 (each
+ *                    chunk drops terms below 2^-73 of its maximum); FP64
+ *                    data: FP64 additions.  NaN for invalid realizations.
  *   plan             nullable handle from ar_plan_create for these offsets on
- *                    this device (NULL: realizations are claimed dynamically
- *                    from a work queue).  Either way the results are the same.
+ *                    this device (NULL: one work item per realization, claimed
+ *                    from a global queue in the workspace; realizations
+ *                    longer than 1024 elements are then reduced by a single
+ *                    warp).  Either way the results are the same.
  *   Realizations with M_b >= 2^31 (or decreasing offsets) are not
  *   processed: AR_STATUS_UNSUPPORTED is raised.
- *   d_work           scratch of ar_select_batched_workspace_size(B) bytes,
- *                    16-byte aligned, zero-filled before its first use;
- *                    every call leaves it zero-filled again (one launch per
- *                    call).  Calls sharing a workspace must not overlap.
+ *   d_work           (plan == NULL only; ignored with a plan) scratch of
+ *                    ar_select_batched_workspace_size(B) = 16 + 32 B bytes,
+ *                    16-byte aligned.  Its first 16 bytes must be zero before
+ *                    the first use and every call leaves them zero again (the
+ *                    claim counter, reset by the launch itself); the rest is
+ *                    rewritten by every call.  Calls sharing a workspace must
+ *                    not overlap.
  *   d_idx, d_stats, d_status   as in ar_select_k (status also collects
  *                    BAD_ALPHA and ALL_ZERO of any realization).
  * ------------------------------------------------------------------- */
@@ -192,15 +201,24 @@ size_t ar_select_batched_workspace_size(int64_t B);
  * ar_plan_create -- tuning handle for repeated ar_select_batched calls on
  * one batch shape (the paper's K realizations of fixed sizes, iterated
  * over SSA steps).  Built on the host from the shape alone (no
- * propensities): the order in which the persistent warps claim the
- * realizations, largest estimated cost first (longest-processing-time-first
- * list scheduling), so that the last claims of a launch are the cheapest.
- * Results are identical with or without a plan.
+ * propensities):
+ *   - the reduction chunks: each realization cut into ceil(M_b / 1024)
+ *     chunks of equal length (16 bytes each);
+ *   - the selection work: ranges of 32 selections.  The costliest
+ *     realizations (estimated cost K_b (0.6 + ln M_b) + 0.05 M_b) are
+ *     assigned to the persistent CTAs of the selection kernel by
+ *     longest-processing-time-first list scheduling (each CTA's home list);
+ *     the cheapest ones, 30% of the estimated cost, form a global queue
+ *     that balances the CTAs' finishing times (32 bytes per range);
+ *   - device scratch for the chunk partials (32 bytes per chunk).
+ * Results are identical with or without a plan.  Calls sharing a plan must
+ * not overlap on the GPU (they share its scratch).
  *   h_offsets, h_out_offsets  [B+1] int64 HOST arrays, as passed (on the
  *                device) to ar_select_batched.  A plan is valid only for
- *                calls whose offsets have exactly these values.
- *   *out         receives the handle.  The plan owns device memory
- *                (4 bytes per realization) until ar_plan_destroy.
+ *                calls whose offsets have exactly these values, on the device
+ *                current when it was built.
+ *   *out         receives the handle; it owns device memory until
+ *                ar_plan_destroy.
  * Errors: AR_ERR_ARG (B <= 0, decreasing offsets, null pointers),
  * AR_ERR_CUDA (allocation or copy failed).
  * ------------------------------------------------------------------- */

@@ -1,21 +1,44 @@
-// ar_select_batched: thousands of realizations with uneven M_b and K_b in one
-// persistent launch.  The paper runs K realizations as K thread blocks of M
-// threads (Section "A GPU acceptance-rejection algorithm"; a 1D grid limited
-// to 65536 blocks, Section "Implementation"; several blocks per realization
-// when M exceeds a block, Discussion).
+// ar_select_batched: thousands of realizations with uneven M_b and K_b.  The
+// paper runs K realizations as K thread blocks of M threads (Section "A GPU
+// acceptance-rejection algorithm"; a 1D grid limited to 65536 blocks, Section
+// "Implementation"; several blocks per realization when M exceeds a block,
+// Discussion).
 //
-// Here every warp of a persistent grid is an independent worker: it claims a
-// realization from a global queue (in the order a plan chose, largest first,
-// so the last claims are the cheap ones), streams its propensities once from
-// HBM with coalesced loads -- computing the exact maximum (the threshold T)
-// on bit patterns and an exact fixed-point sum -- and then runs the
-// warp-level selection engine of select.cuh on its K_b selections.  The
-// engine's gathers hit the realization's lines in L1 (read-only loads), so no
-// staging copy or CTA-wide barrier is needed, and warps never wait for one
-// another: a warp that finishes early claims the next realization.
+// Three launches on the caller's stream:
+//
+//   k_bound_reg / k_batched_bound   per-chunk partial results: maximum
+//       (exact, on bit patterns), validity and exact sum of chunks of at most
+//       1024 propensities (with a plan: each realization cut into equal
+//       chunks).  Each warp streams its chunks with 16-byte vector loads into
+//       registers, one chunk ahead of the one it reduces, and only touches
+//       the 16-byte groups a chunk has.  A chunk's sum is an exact integer in
+//       units of a power of two set by the chunk's maximum: when every
+//       non-zero value lies within 2^24 of that maximum (the common case) it
+//       comes from packed FP32 additions that are exact by construction
+//       (three-level splitting against power-of-two constants), otherwise
+//       from integer windows.  GB300's FP64 rate is a small fraction of its
+//       FP32 and integer rates, so no FP64 operation touches the elements.
+//   k_batched_combine   one warp per realization: T_b = the maximum of its
+//       chunk maxima, the chunk sums aligned and added exactly in 128 bits and
+//       rounded once to FP64, the status.
+//   k_batched_select    the selections.  A plan gives each persistent CTA a
+//       home list of its realizations (the costliest ones, by
+//       longest-processing-time-first list scheduling) in ranges of 32
+//       selections claimed in order from a shared-memory counter, so the
+//       warps of an SM work on one or two realizations at a time and the
+//       gathers hit L1; the cheapest realizations form a global queue of
+//       32-selection ranges that the warps drain once their home list is
+//       empty.  A lane that finishes a selection takes the next one at once,
+//       so no warp waits for the slowest selection of a realization.  Per
+//       round a lane evaluates U Philox blocks (2U trials) of its own
+//       selection with all 2U gathers in flight at once; only when no work is
+//       left do the last selections share lanes.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <numeric>
+#include <queue>
+#include <utility>
 #include <vector>
 
 #include "device.cuh"
@@ -25,19 +48,55 @@
 namespace gbar {
 namespace {
 
-constexpr int kWarps = 16;  // warps per CTA
+constexpr int kWarps = 16;  // selection kernel
 constexpr int kNT = kWarps * 32;
 constexpr int kCtasPerSm = 2;
-constexpr uint32_t kFxBlock = 16384;  // per-lane fixed-point block (< 2^14 terms of < 2^48)
+constexpr int kBWarps = 8;  // reduction kernels
+constexpr int kBNT = kBWarps * 32;
+constexpr int kBCtasPerSm = 2;
+constexpr uint32_t kChunk = 1024;  // reduction chunk (elements)
+constexpr int kVPL = kChunk / 32;  // elements per lane (register path)
+constexpr uint32_t kSItem = 32;     // selections per home work item
+constexpr uint32_t kGItem = 32;     // selections per global-queue work item
+constexpr double kGlobalShare = 0.3;  // estimated cost left to the global queue
+constexpr int kU = 2;               // Philox blocks per lane per round
 
-struct BatchWork {
-  uint32_t queue;  // next position of the processing order to claim
-  uint32_t done;   // CTAs finished
+// ---- plan-built work items -------------------------------------------------
+struct RItem {  // one reduction chunk: alpha_cat[e0, e0 + n)
+  int64_t e0;
+  uint32_t n;
+  uint32_t pad;
+};
+struct RInfo {  // chunk partials of one realization
+  uint32_t p0, nch;
+};
+struct SItem {     // selections [s0, s1) of realization b
+  int64_t a0, o0;  // first element / first output index of the realization
+  uint32_t M, b, s0, s1;
+};
+struct Part {                 // a chunk's partial result
+  unsigned long long hi, lo;  // FP32 data: exact sum (hi:lo) 2^e; FP64: lo = sum bits
+  unsigned long long vmax;    // maximum (bit pattern)
+  int32_t e;
+  uint32_t bad;               // 1: invalid value, 2: unusable offsets
+};
+static_assert(sizeof(Part) == 32, "Part layout");
+
+struct Scratch {
+  uint32_t squeue;  // next global work item to claim
+  uint32_t sdone;   // CTAs finished (the last one resets squeue)
   uint32_t pad[2];
 };
 
-struct BatchParams {
-  const uint32_t* order;  // processing order (plan), NULL: 0..B-1
+struct Params {
+  const RItem* ritems;   // NULL: one item per realization, read from the offsets
+  const RInfo* rinfo;    // [B] (plan)
+  const SItem* sitems;   // NULL: one item per realization, global queue
+  const uint32_t* scta;  // [grid + 1] home lists of the CTAs (plan)
+  uint32_t nr;
+  uint32_t gq0, gq1;     // global-queue items [gq0, gq1) of sitems (plan)
+  Part* parts;           // [NR] (plan) or [B]
+  Scratch* scratch;
   const unsigned char* alpha;
   const int64_t* offsets;
   const int64_t* out_offsets;
@@ -45,175 +104,841 @@ struct BatchParams {
   int32_t* idx;
   ar_stats* stats;
   uint32_t* status;
-  BatchWork* work;
   unsigned long long cap;
   uint32_t B;
   uint32_t sel_base;
   uint32_t b_base;
   uint32_t k0, k1;
+  uint32_t vec_ok;  // alpha_cat is 16-byte aligned (vector loads)
 };
 
-// Warp reduction of one realization: exact maximum (on bit patterns),
-// validity, and the FP64-grade sum.  Every lane returns T and the sum.
-template <typename TS>
-__device__ __forceinline__ void warp_bound(const TS* __restrict__ a, uint32_t M, double& T,
-                                           double& sum, bool& bad) {
-  const uint32_t lane = threadIdx.x & 31u;
-  if constexpr (sizeof(TS) == 4) {
-    const uint32_t* u = reinterpret_cast<const uint32_t*>(a);
-    MaxF32 mx;
-    uint32_t i = lane;
-    for (; i + 96 < M; i += 128) {
-      const uint32_t x0 = __ldg(u + i), x1 = __ldg(u + i + 32), x2 = __ldg(u + i + 64),
-                     x3 = __ldg(u + i + 96);
-      mx.add(x0);
-      mx.add(x1);
-      mx.add(x2);
-      mx.add(x3);
-    }
-    for (; i < M; i += 32) mx.add(__ldg(u + i));
-    mx.smax = warp_max_i32(mx.smax);
-    mx.umax = warp_max_u32(mx.umax);
-    bad = mx.bad();
-    const uint32_t mb = mx.value_bits();
-    T = (double)__uint_as_float(mb);
-    const int e_ref = fx_eref(mb);
-    // second pass (L1 hits): exact per lane, in blocks of kFxBlock elements
-    double lane_sum = 0.0;
-    FxSum fx;
-    uint32_t in_block = 0;
-    i = lane;
-    for (; i + 96 < M; i += 128) {
-      const uint32_t x0 = __ldg(u + i), x1 = __ldg(u + i + 32), x2 = __ldg(u + i + 64),
-                     x3 = __ldg(u + i + 96);
-      fx.add(x0, e_ref);
-      fx.add(x1, e_ref);
-      fx.add(x2, e_ref);
-      fx.add(x3, e_ref);
-      if ((in_block += 4) >= kFxBlock) {
-        lane_sum = __dadd_rn(lane_sum, fx.to_double(e_ref));
-        fx = FxSum();
-        in_block = 0;
+// ===========================================================================
+// Exact integer sums
+// ===========================================================================
+struct U128 {
+  unsigned long long hi = 0, lo = 0;
+};
+__device__ __forceinline__ U128 add128(U128 x, U128 y) {
+  U128 r;
+  r.lo = x.lo + y.lo;
+  r.hi = x.hi + y.hi + (r.lo < x.lo ? 1ull : 0ull);
+  return r;
+}
+__device__ __forceinline__ U128 shl128(unsigned long long x, int s) {  // 0 <= s < 64
+  U128 r;
+  r.lo = x << s;
+  r.hi = s == 0 ? 0ull : (x >> (64 - s));
+  return r;
+}
+__device__ __forceinline__ U128 shr128(U128 x, int s) {  // s >= 0
+  U128 r;
+  if (s >= 128) return r;
+  if (s >= 64) {
+    r.lo = x.hi >> (s - 64);
+    return r;
+  }
+  if (s == 0) return x;
+  r.lo = (x.lo >> s) | (x.hi << (64 - s));
+  r.hi = x.hi >> s;
+  return r;
+}
+__device__ __forceinline__ U128 warp_sum128(U128 x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    U128 y;
+    y.hi = __shfl_xor_sync(kFull, x.hi, o);
+    y.lo = __shfl_xor_sync(kFull, x.lo, o);
+    x = add128(x, y);
+  }
+  return x;
+}
+
+// x * 2^e rounded to the nearest double (ties to even), integer arithmetic
+// only.  The result is a normal double for every FP32 input here.
+__device__ double u128_to_double(U128 x, int e) {
+  if (x.hi == 0 && x.lo == 0) return 0.0;
+  const int nbits = x.hi ? 128 - __clzll((long long)x.hi) : 64 - __clzll((long long)x.lo);
+  int ex = e + nbits - 1;  // exponent of the leading bit
+  unsigned long long mant;
+  if (nbits <= 53) {
+    mant = x.lo << (53 - nbits);
+  } else {
+    const int sh = nbits - 53;  // bits below the kept 53 (1..75)
+    mant = shr128(x, sh).lo;
+    const int hb = sh - 1;      // the half bit
+    const bool half = hb >= 64 ? ((x.hi >> (hb - 64)) & 1ull) : ((x.lo >> hb) & 1ull);
+    const bool sticky = hb >= 64 ? (x.lo != 0 || (x.hi & ((1ull << (hb - 64)) - 1ull)) != 0)
+                                 : (x.lo & ((1ull << hb) - 1ull)) != 0;
+    if (half && (sticky || (mant & 1ull))) {
+      ++mant;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++ex;
       }
     }
-    for (; i < M; i += 32) fx.add(__ldg(u + i), e_ref);
-    if (M < 65536u) {
-      // fewer than 2^16 terms of < 2^48 in the whole warp: exact integer sum
-      fx.warp_reduce();
-      sum = fx.to_double(e_ref);
-    } else {
-      lane_sum = __dadd_rn(lane_sum, fx.to_double(e_ref));
-      sum = warp_sum_f64(lane_sum);
+  }
+  const unsigned long long bits =
+      ((unsigned long long)(ex + 1023) << 52) | (mant & 0xfffffffffffffull);
+  return __longlong_as_double((long long)bits);
+}
+
+// Exact fixed-point windows of non-negative FP32 values, e_ref the biased
+// exponent of their maximum (at least 1); value = m 2^(e - 150), d = e_ref - e:
+//   d <= 24: a1 += m << (24 - d)   (unit 2^(e_ref - 174))
+//   d <= 49: a2 += m << (49 - d)   (unit 2^(e_ref - 199))
+//   d <= 74: a3 += m << (74 - d)   (unit 2^(e_ref - 224))
+// Smaller values (below 2^-73 of the maximum each) are dropped.  Every term
+// is < 2^48, so each window is exact for up to 2^15 terms; the total is
+// (a1 2^50 + a2 2^25 + a3) 2^(e_ref - 224), below 2^108 units for a chunk.
+struct Fx3 {
+  unsigned long long a1 = 0, a2 = 0, a3 = 0;
+  __device__ __forceinline__ void add(uint32_t bits, int e_ref) {
+    bits &= 0x7fffffffu;
+    int e = (int)(bits >> 23);
+    uint32_t m = bits & 0x7fffffu;
+    if (e) m |= 0x800000u; else e = 1;
+    const int d = e_ref - e;
+    if (d <= 24) a1 += (unsigned long long)m << (24 - d);
+    else if (d <= 49) a2 += (unsigned long long)m << (49 - d);
+    else if (d <= 74) a3 += (unsigned long long)m << (74 - d);
+  }
+  __device__ __forceinline__ U128 total() const {
+    return add128(shl128(a1, 50), add128(shl128(a2, 25), U128{0ull, a3}));
+  }
+};
+
+// 2^k as an FP32 value, -126 <= k <= 127
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((k + 127) << 23); }
+// f 2^s for an FP32 f that is an integer multiple of 2^-s with |f 2^s| <= 2^24,
+// -126 <= s / 2 and s - s / 2 <= 127 (two exact power-of-two scalings)
+__device__ __forceinline__ long long scaled_int(float f, int s) {
+  const int s1 = s / 2;
+  return __float2ll_rn(__fmul_rn(__fmul_rn(f, pow2f(s1)), pow2f(s - s1)));
+}
+
+// ===========================================================================
+// Reduction kernels
+// ===========================================================================
+
+// Partial result of N FP32 values (bit patterns) held in registers plus one
+// extra value per lane; zeros are neutral.  All lanes return it.
+template <int N>
+__device__ __forceinline__ Part reduce_f32(const uint32_t (&v)[N], uint32_t xs) {
+  static_assert(N % 2 == 0 && N / 2 + 1 <= 33, "terms per accumulator");
+  // maximum of the raw bits; an invalid value or -0 pushes it to >= 2^31 or
+  // into the inf/NaN range and sends the chunk to the exact slow path
+  uint32_t umax = xs, umin1 = xs - 1u;  // umin1: smallest non-zero value - 1
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    umax = max(umax, v[k]);
+    umin1 = min(umin1, v[k] - 1u);
+  }
+  umax = __reduce_max_sync(kFull, umax);
+  umin1 = __reduce_min_sync(kFull, umin1);
+  Part r;
+  const int e_ref = max((int)(umax >> 23), 1);
+  if (umax < 0x7f800000u && e_ref >= 25 && e_ref <= 248 &&
+      umin1 >= ((uint32_t)(e_ref - 24) << 23) - 1u) {
+    // Every non-zero value x lies in [2^24 U, 2^48 U), U = 2^(e_ref - 174),
+    // and is a multiple of U.  x = h + m + r with h a multiple of 2^30 U,
+    // m of 2^12 U, |r| <= 2^11 U, each split exact (round-to-nearest against
+    // 1.5 2^53 U and 1.5 2^35 U, then exact differences); at most 33 terms
+    // per accumulator keep every running sum below 2^24 units of its level,
+    // so the three FP32 sums are exact.
+    const float C1 = __int_as_float(((e_ref + 6) << 23) | 0x400000);
+    const float C2 = __int_as_float(((e_ref - 12) << 23) | 0x400000);
+    const float2 c1 = make_float2(C1, C1), n1 = make_float2(-C1, -C1);
+    const float2 c2 = make_float2(C2, C2), n2 = make_float2(-C2, -C2);
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 s1 = make_float2(0.f, 0.f), s2 = s1, s3 = s1;
+    auto split = [&](uint32_t a, uint32_t b) {
+      const float2 x = make_float2(__uint_as_float(a), __uint_as_float(b));
+      const float2 h = __fadd2_rn(__fadd2_rn(x, c1), n1);
+      const float2 l = __ffma2_rn(h, m1, x);  // x - h
+      const float2 m = __fadd2_rn(__fadd2_rn(l, c2), n2);
+      s1 = __fadd2_rn(s1, h);
+      s2 = __fadd2_rn(s2, m);
+      s3 = __fadd2_rn(s3, __ffma2_rn(m, m1, l));  // l - m
+    };
+#pragma unroll
+    for (int k = 0; k < N; k += 2) split(v[k], v[k + 1]);
+    split(xs, 0u);
+    const long long S =
+        ((scaled_int(s1.x, 144 - e_ref) + scaled_int(s1.y, 144 - e_ref)) << 30) +
+        ((scaled_int(s2.x, 162 - e_ref) + scaled_int(s2.y, 162 - e_ref)) << 12) +
+        scaled_int(s3.x, 174 - e_ref) + scaled_int(s3.y, 174 - e_ref);
+    const unsigned long long X = warp_sum_u64((unsigned long long)S);  // < 2^58
+    const U128 x50 = shl128(X, 50);
+    r.hi = x50.hi;
+    r.lo = x50.lo;
+    r.vmax = umax;
+    r.e = e_ref - 224;
+    r.bad = 0u;
+    return r;
+  }
+  // exact slow path: validity on signed/unsigned maxima, integer windows
+  MaxF32 mx;
+#pragma unroll
+  for (int k = 0; k < N; ++k) mx.add(v[k]);
+  mx.add(xs);
+  mx.smax = warp_max_i32(mx.smax);
+  mx.umax = warp_max_u32(mx.umax);
+  const uint32_t vb = mx.value_bits();
+  const int e2 = fx_eref(vb);
+  Fx3 fx;
+#pragma unroll
+  for (int k = 0; k < N; ++k) fx.add(v[k], e2);
+  fx.add(xs, e2);
+  fx.a1 = warp_sum_u64(fx.a1);
+  fx.a2 = warp_sum_u64(fx.a2);
+  fx.a3 = warp_sum_u64(fx.a3);
+  const U128 X = fx.total();
+  r.hi = X.hi;
+  r.lo = X.lo;
+  r.vmax = vb;
+  r.e = e2 - 224;
+  r.bad = mx.bad() ? 1u : 0u;
+  return r;
+}
+
+// Register path: chunk [e0, e0 + n), n <= 1024, loaded straight into lane
+// registers (16-byte groups when the buffer is aligned, head and tail
+// elements by lanes 0-2 and 3-5).
+__device__ __forceinline__ Part chunk_f32(const uint32_t* __restrict__ u, int64_t e0, uint32_t n,
+                                          bool vec_ok) {
+  const uint32_t lane = threadIdx.x & 31u;
+  int64_t g0 = (e0 + 3) & ~int64_t(3), g1 = (e0 + n) & ~int64_t(3);
+  if (!vec_ok || g1 < g0) g0 = g1 = e0;  // no vector part
+  uint32_t v[kVPL];
+  if (vec_ok) {
+    const uint32_t ngroups = (uint32_t)((g1 - g0) >> 2);
+    const uint4* gp = reinterpret_cast<const uint4*>(u + g0);
+#pragma unroll
+    for (int k = 0; k < kVPL / 4; ++k) {
+      const uint32_t g = lane + 32u * k;
+      uint4 x = make_uint4(0u, 0u, 0u, 0u);
+      if (g < ngroups) x = __ldg(gp + g);
+      v[4 * k] = x.x;
+      v[4 * k + 1] = x.y;
+      v[4 * k + 2] = x.z;
+      v[4 * k + 3] = x.w;
     }
   } else {
-    const unsigned long long* u = reinterpret_cast<const unsigned long long*>(a);
-    MaxF64 mx;
-    double s = 0.0;
-    for (uint32_t i = lane; i < M; i += 32) {
-      const unsigned long long x = __ldg(u + i);
-      mx.add(x);
-      s = __dadd_rn(s, __longlong_as_double((long long)x));
+#pragma unroll
+    for (int k = 0; k < kVPL; ++k) {
+      const uint32_t i = lane + 32u * k;
+      v[k] = i < n ? __ldg(u + e0 + i) : 0u;
     }
-    mx.smax = warp_max_i64(mx.smax);
-    mx.umax = warp_max_u64(mx.umax);
-    bad = mx.bad();
-    T = __longlong_as_double((long long)mx.value_bits());
-    sum = warp_sum_f64(s);
+  }
+  const int64_t hn = g0 - e0, tn = vec_ok ? e0 + n - g1 : 0;
+  uint32_t xs = 0u;
+  if (lane < 3 && (int64_t)lane < hn) xs = __ldg(u + e0 + lane);
+  else if (lane >= 3 && lane < 6 && (int64_t)(lane - 3) < tn) xs = __ldg(u + g1 + (lane - 3));
+  return reduce_f32<kVPL>(v, xs);
+}
+
+// Realizations longer than a chunk (calls without a plan): two passes over
+// global memory, per-lane integer windows flushed every 2^15 terms.
+__device__ Part long_f32(const uint32_t* __restrict__ w, uint32_t n) {
+  const uint32_t lane = threadIdx.x & 31u;
+  MaxF32 mx;
+  for (uint32_t i = lane; i < n; i += 32) mx.add(__ldg(w + i));
+  mx.smax = warp_max_i32(mx.smax);
+  mx.umax = warp_max_u32(mx.umax);
+  const uint32_t vb = mx.value_bits();
+  const int e_ref = fx_eref(vb);
+  U128 acc;
+  Fx3 fx;
+  uint32_t in_block = 0;
+  for (uint32_t i = lane; i < n; i += 32) {
+    fx.add(__ldg(w + i), e_ref);
+    if (++in_block == 32768u) {
+      acc = add128(acc, fx.total());
+      fx = Fx3();
+      in_block = 0;
+    }
+  }
+  acc = add128(acc, fx.total());
+  // one bit down: 2^31 values below 2^98 units each would overflow 128 bits
+  const U128 X = warp_sum128(shr128(acc, 1));
+  Part r;
+  r.hi = X.hi;
+  r.lo = X.lo;
+  r.vmax = vb;
+  r.e = e_ref - 223;
+  r.bad = mx.bad() ? 1u : 0u;
+  return r;
+}
+
+__device__ Part reduce_f64(const unsigned long long* __restrict__ w, uint32_t n) {
+  const uint32_t lane = threadIdx.x & 31u;
+  MaxF64 mx;
+  double s = 0.0;
+  for (uint32_t i = lane; i < n; i += 32) {
+    const unsigned long long x = __ldg(w + i);
+    mx.add(x);
+    s = __dadd_rn(s, __longlong_as_double((long long)x));
+  }
+  mx.smax = warp_max_i64(mx.smax);
+  mx.umax = warp_max_u64(mx.umax);
+  Part r;
+  r.hi = 0ull;
+  r.lo = (unsigned long long)__double_as_longlong(warp_sum_f64(s));
+  r.vmax = mx.value_bits();
+  r.e = 0;
+  r.bad = mx.bad() ? 1u : 0u;
+  return r;
+}
+
+__device__ __forceinline__ void store_part(Part* dst, const Part& r) {
+  if ((threadIdx.x & 31u) == 0) *dst = r;
+}
+
+// reduce with only the first kq groups (of 4 values) per lane live
+template <int N>
+__device__ __forceinline__ Part reduce_f32q(const uint32_t (&v)[N], uint32_t xs, int kq) {
+  uint32_t umax = xs, umin1 = xs - 1u;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    if (k / 4 < kq) {
+      umax = max(umax, v[k]);
+      umin1 = min(umin1, v[k] - 1u);
+    }
+  }
+  umax = __reduce_max_sync(kFull, umax);
+  umin1 = __reduce_min_sync(kFull, umin1);
+  Part r;
+  const int e_ref = max((int)(umax >> 23), 1);
+  if (umax < 0x7f800000u && e_ref >= 25 && e_ref <= 248 &&
+      umin1 >= ((uint32_t)(e_ref - 24) << 23) - 1u) {
+    const float C1 = __int_as_float(((e_ref + 6) << 23) | 0x400000);
+    const float C2 = __int_as_float(((e_ref - 12) << 23) | 0x400000);
+    const float2 c1 = make_float2(C1, C1), n1 = make_float2(-C1, -C1);
+    const float2 c2 = make_float2(C2, C2), n2 = make_float2(-C2, -C2);
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 s1 = make_float2(0.f, 0.f), s2 = s1, s3 = s1;
+    auto split = [&](uint32_t a, uint32_t b) {
+      const float2 x = make_float2(__uint_as_float(a), __uint_as_float(b));
+      const float2 h = __fadd2_rn(__fadd2_rn(x, c1), n1);
+      const float2 l = __ffma2_rn(h, m1, x);
+      const float2 m = __fadd2_rn(__fadd2_rn(l, c2), n2);
+      s1 = __fadd2_rn(s1, h);
+      s2 = __fadd2_rn(s2, m);
+      s3 = __fadd2_rn(s3, __ffma2_rn(m, m1, l));
+    };
+#pragma unroll
+    for (int k = 0; k < N; k += 2)
+      if (k / 4 < kq) split(v[k], v[k + 1]);
+    split(xs, 0u);
+    const int t1 = 144 - e_ref, t2 = 162 - e_ref, t3 = 174 - e_ref;
+    const float a1 = pow2f(t1 / 2), b1 = pow2f(t1 - t1 / 2);
+    const float a2 = pow2f(t2 / 2), b2 = pow2f(t2 - t2 / 2);
+    const float a3 = pow2f(t3 / 2), b3 = pow2f(t3 - t3 / 2);
+    auto cv = [](float f, float a, float b) { return __float2int_rn(__fmul_rn(__fmul_rn(f, a), b)); };
+    const long long S = ((long long)(cv(s1.x, a1, b1) + cv(s1.y, a1, b1)) << 30) +
+                        ((long long)(cv(s2.x, a2, b2) + cv(s2.y, a2, b2)) << 12) +
+                        (long long)(cv(s3.x, a3, b3) + cv(s3.y, a3, b3));
+    const unsigned long long X = warp_sum_u64((unsigned long long)S);
+    const U128 x50 = shl128(X, 50);
+    r.hi = x50.hi;
+    r.lo = x50.lo;
+    r.vmax = umax;
+    r.e = e_ref - 224;
+    r.bad = 0u;
+    return r;
+  }
+  return reduce_f32<N>(v, xs);  // slow path (zeros beyond kq are loaded as zeros)
+}
+
+__global__ void __launch_bounds__(kBNT, kBCtasPerSm) k_bound_reg(const Params p) {
+  const uint32_t stride = gridDim.x * kBWarps;
+  uint32_t it = blockIdx.x * kBWarps + (threadIdx.x >> 5);
+  const uint32_t* u = reinterpret_cast<const uint32_t*>(p.alpha);
+  if (it >= p.nr) return;
+  const uint32_t lane = threadIdx.x & 31u;
+  auto load = [&](const RItem& d, uint32_t (&v)[kVPL], uint32_t& xs) -> int {
+    int64_t g0 = (d.e0 + 3) & ~int64_t(3), g1 = (d.e0 + d.n) & ~int64_t(3);
+    if (g1 < g0) g0 = g1 = d.e0;
+    const uint32_t ngroups = (uint32_t)((g1 - g0) >> 2);
+    const int kq = (int)((ngroups + 31u) >> 5);
+    const uint4* gp = reinterpret_cast<const uint4*>(u + g0);
+#pragma unroll
+    for (int k = 0; k < kVPL / 4; ++k) {
+      const uint32_t g = lane + 32u * k;
+      uint4 x = make_uint4(0u, 0u, 0u, 0u);
+      if (k < kq && g < ngroups) x = __ldg(gp + g);
+      v[4 * k] = x.x; v[4 * k + 1] = x.y; v[4 * k + 2] = x.z; v[4 * k + 3] = x.w;
+    }
+    const int64_t hn = g0 - d.e0, tn = d.e0 + d.n - g1;
+    xs = 0u;
+    if (lane < 3 && (int64_t)lane < hn) xs = __ldg(u + d.e0 + lane);
+    else if (lane >= 3 && lane < 6 && (int64_t)(lane - 3) < tn) xs = __ldg(u + g1 + (lane - 3));
+    return kq;
+  };
+  uint32_t va[kVPL], vb[kVPL], xa, xb;
+  int qa, qb = 0;
+  RItem d = p.ritems[it];
+  qa = load(d, va, xa);
+  if (it + stride < p.nr) d = p.ritems[it + stride];
+  for (;;) {
+    uint32_t nx = it + stride;
+    if (nx < p.nr) {
+      qb = load(d, vb, xb);
+      if (nx + stride < p.nr) d = p.ritems[nx + stride];
+    }
+    store_part(p.parts + it, reduce_f32q<kVPL>(va, xa, qa));
+    if (nx >= p.nr) return;
+    it = nx;
+    nx = it + stride;
+    if (nx < p.nr) {
+      qa = load(d, va, xa);
+      if (nx + stride < p.nr) d = p.ritems[nx + stride];
+    }
+    store_part(p.parts + it, reduce_f32q<kVPL>(vb, xb, qb));
+    if (nx >= p.nr) return;
+    it = nx;
+  }
+}
+
+// Register path: FP64 data, unaligned FP32 buffers, calls without a plan.
+template <typename TS>
+__global__ void __launch_bounds__(kBNT) k_batched_bound(const Params p) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t stride = gridDim.x * kBWarps;
+  const uint32_t nitems = p.ritems ? p.nr : p.B;
+  for (uint32_t it = blockIdx.x * kBWarps + (threadIdx.x >> 5); it < nitems; it += stride) {
+    int64_t e0;
+    uint32_t n;
+    if (p.ritems) {
+      e0 = p.ritems[it].e0;
+      n = p.ritems[it].n;
+    } else {
+      int64_t v = 0;
+      if (lane < 2) v = __ldg(p.offsets + it + lane);
+      const int64_t a0 = __shfl_sync(kFull, v, 0), a1 = __shfl_sync(kFull, v, 1);
+      e0 = a0;
+      n = (a1 < a0 || a1 - a0 >= (1ll << 31)) ? 0xffffffffu : (uint32_t)(a1 - a0);
+    }
+    Part r;
+    if (n == 0xffffffffu) {  // unusable offsets
+      r.hi = r.lo = r.vmax = 0ull;
+      r.e = 0;
+      r.bad = 2u;
+    } else if constexpr (sizeof(TS) == 4) {
+      const uint32_t* u = reinterpret_cast<const uint32_t*>(p.alpha);
+      r = n <= kChunk ? chunk_f32(u, e0, n, p.vec_ok != 0) : long_f32(u + e0, n);
+    } else {
+      r = reduce_f64(reinterpret_cast<const unsigned long long*>(p.alpha) + e0, n);
+    }
+    store_part(p.parts + it, r);
+  }
+}
+
+// One warp per realization: bound, total and status from its chunk partials.
+template <typename TS>
+__global__ void __launch_bounds__(kBNT) k_batched_combine(const Params p) {
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t st_acc = 0;
+  for (uint32_t b = blockIdx.x * kBWarps + (threadIdx.x >> 5); b < p.B;
+       b += gridDim.x * kBWarps) {
+    uint32_t p0 = b, nch = 1;
+    if (p.rinfo) {
+      p0 = p.rinfo[b].p0;
+      nch = p.rinfo[b].nch;
+    }
+    unsigned long long vm = 0;
+    uint32_t bd = 0;
+    int emax = INT32_MIN;
+    for (uint32_t k = lane; k < nch; k += 32) {
+      const Part& q = p.parts[p0 + k];
+      const unsigned long long x = q.vmax;
+      vm = x > vm ? x : vm;
+      bd |= q.bad;
+      emax = max(emax, q.e);
+    }
+    vm = warp_max_u64(vm);
+    bd = __reduce_or_sync(kFull, bd);
+    double sum = 0.0;
+    if (!bd) {
+      if constexpr (sizeof(TS) == 4) {
+        // align every chunk to one bit above the largest exponent (chunk
+        // sums are < 2^108 units, so 2^21 of them fit in 128 bits; bits
+        // below 2^-96 of the maximum are dropped), add exactly, round once
+        emax = __reduce_max_sync(kFull, emax) + 1;
+        U128 acc;
+        for (uint32_t k = lane; k < nch; k += 32) {
+          const Part& q = p.parts[p0 + k];
+          U128 y;
+          y.hi = q.hi;
+          y.lo = q.lo;
+          acc = add128(acc, shr128(y, emax - q.e));
+        }
+        acc = warp_sum128(acc);
+        if (lane == 0) sum = u128_to_double(acc, emax);
+      } else {
+        if (lane == 0)
+          for (uint32_t k = 0; k < nch; ++k)
+            sum = __dadd_rn(sum, __longlong_as_double((long long)p.parts[p0 + k].lo));
+      }
+    }
+    if (lane == 0) {
+      double* o = p.bound_sum + 2 * (size_t)b;
+      if (bd) {
+        st_acc |= (bd & 1u) ? AR_STATUS_BAD_ALPHA : 0u;
+        st_acc |= (bd & 2u) ? AR_STATUS_UNSUPPORTED : 0u;
+        o[0] = o[1] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: no selections
+      } else {
+        o[0] = sizeof(TS) == 4 ? (double)__uint_as_float((uint32_t)vm)
+                               : __longlong_as_double((long long)vm);
+        o[1] = sum;
+      }
+    }
+  }
+  st_acc = __reduce_or_sync(kFull, st_acc);
+  if (lane == 0 && st_acc) atomicOr(p.status, st_acc);
+}
+
+// ===========================================================================
+// Selection kernel
+// ===========================================================================
+template <typename TS>
+struct Lane {
+  bool act = false;
+  uint32_t sel = 0, cnt = 0, M = 0, b = 0;
+  const TS* a = nullptr;
+  int32_t* out = nullptr;
+  float Tf = 0.f;
+  double T = 0.0;
+};
+
+template <typename TS>
+struct WItem {  // the warp's current item (identical in every lane)
+  uint32_t b = 0, s = 0, s1 = 0, M = 0;
+  const TS* a = nullptr;
+  int32_t* out = nullptr;
+  float Tf = 0.f;
+  double T = 0.0;
+};
+
+// The comparison operand alpha_j: FP32 or FP64 per the comparison precision.
+template <typename TS, int CMP>
+__device__ __forceinline__ auto load_alpha(const TS* a, uint32_t j) {
+  if constexpr (CMP == AR_CMP_F32) {
+    if constexpr (sizeof(TS) == 4) return __ldg(a + j);
+    else return __double2float_rn(__ldg(a + j));
+  } else {
+    return (double)__ldg(a + j);
+  }
+}
+
+// Evaluates Philox blocks cnt .. cnt + kU - 1 of selection (sel, b): returns
+// the lowest accepted trial offset (0 .. 2kU - 1, or -1) among the first
+// `nvalid` trials and its candidate.  All gathers are issued before any test.
+template <typename TS, int CMP>
+__device__ __forceinline__ int eval_blocks(const Params& p, uint32_t cnt, uint32_t sel, uint32_t b,
+                                           uint32_t M, const TS* a, float Tf, double T,
+                                           uint32_t nvalid, uint32_t& jh) {
+  uint4 w[kU];
+#pragma unroll
+  for (int u = 0; u < kU; ++u)
+    w[u] = philox10(make_uint4(cnt + u, p.sel_base + sel, p.b_base + b, 0u), p.k0, p.k1);
+  uint32_t j[2 * kU];
+#pragma unroll
+  for (int u = 0; u < kU; ++u) {
+    j[2 * u] = candidate(w[u].x, M);
+    j[2 * u + 1] = candidate(w[u].z, M);
+  }
+  decltype(load_alpha<TS, CMP>(a, 0u)) x[2 * kU];
+#pragma unroll
+  for (int t = 0; t < 2 * kU; ++t) x[t] = load_alpha<TS, CMP>(a, j[t]);
+  int hit = -1;
+#pragma unroll
+  for (int t = 2 * kU - 1; t >= 0; --t) {
+    const uint32_t wu = (t & 1) ? w[t >> 1].w : w[t >> 1].y;
+    bool acc;
+    if constexpr (CMP == AR_CMP_F32) acc = accept_f32(wu, Tf, x[t]);
+    else acc = accept_f64(wu, T, x[t]);
+    if ((uint32_t)t < nvalid && acc) {
+      hit = t;
+      jh = j[t];
+    }
+  }
+  return hit;
+}
+
+// Work claiming of one warp: the CTA's home list through a shared-memory
+// counter, then the global queue, whose next ticket is claimed one item
+// ahead so that the atomic's latency overlaps the current item.
+struct Claimer {
+  bool home = true;
+  bool pref = false;  // lane 0: `ticket` holds an unused global ticket
+  uint32_t ticket = 0;
+};
+
+// Claims the next selection item and gathers what the warp needs about it;
+// returns false when no work is left.  Realizations whose bound is unusable
+// get their indices set to M here and are skipped.
+template <typename TS, int CMP>
+__device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Claimer& cl,
+                          WItem<TS>& w, uint32_t& st_acc) {
+  const uint32_t lane = threadIdx.x & 31u;
+  for (;;) {
+    uint32_t i = 0;
+    bool ok = false;
+    if (p.sitems && cl.home) {
+      if (lane == 0) i = atomicAdd(s_queue, 1u);
+      i = __shfl_sync(kFull, i, 0);
+      ok = i < q_end;
+      if (!ok) cl.home = false;
+    }
+    if (!ok) {
+      const uint32_t qb = p.sitems ? p.gq0 : 0u, qe = p.sitems ? p.gq1 : p.B;
+      if (lane == 0) {
+        if (!cl.pref) cl.ticket = atomicAdd(&p.scratch->squeue, 1u);
+        i = qb + cl.ticket;
+        cl.pref = false;
+        if (i < qe) {
+          cl.ticket = atomicAdd(&p.scratch->squeue, 1u);
+          cl.pref = true;
+        }
+      }
+      i = __shfl_sync(kFull, i, 0);
+      if (i >= qe) return false;
+    }
+    int64_t a0 = 0, o0 = 0;
+    uint32_t M = 0, b = 0, s0 = 0, s1 = 0;
+    if (p.sitems) {
+      const SItem& si = p.sitems[i];
+      a0 = si.a0;
+      o0 = si.o0;
+      M = si.M;
+      b = si.b;
+      s0 = si.s0;
+      s1 = si.s1;
+    } else {
+      b = i;
+      int64_t v = 0;
+      if (lane < 2) v = __ldg(p.offsets + b + lane);
+      else if (lane < 4) v = __ldg(p.out_offsets + b + lane - 2);
+      a0 = __shfl_sync(kFull, v, 0);
+      const int64_t a1 = __shfl_sync(kFull, v, 1);
+      o0 = __shfl_sync(kFull, v, 2);
+      const int64_t o1 = __shfl_sync(kFull, v, 3);
+      M = (a1 < a0 || a1 - a0 >= (1ll << 31)) ? 0x7fffffffu : (uint32_t)(a1 - a0);
+      s0 = 0;
+      s1 = o1 > o0 ? (uint32_t)(o1 - o0) : 0u;
+    }
+    // the bound written by k_batched_combine (NaN: unusable realization)
+    const double T = __ldcg(p.bound_sum + 2 * (size_t)b);
+    const float Tf = sizeof(TS) == 4 ? (float)T : __double2float_rn(T);
+    int32_t* out = p.idx + o0;
+    uint32_t st = 0;
+    if (T != T) st = 1;                          // raised by k_batched_combine
+    else if (T == 0.0) st = AR_STATUS_ALL_ZERO;  // the paper's rejection case
+    else if (CMP == AR_CMP_F32 && isinf(Tf)) st = AR_STATUS_BAD_BOUND;
+    if (st) {
+      if (st != 1 && s1 > s0) st_acc |= st;
+      for (uint32_t k = s0 + lane; k < s1; k += 32) out[k] = (int32_t)M;
+      continue;
+    }
+    w.b = b;
+    w.s = s0;
+    w.s1 = s1;
+    w.M = M;
+    w.a = reinterpret_cast<const TS*>(p.alpha) + a0;
+    w.out = out;
+    w.Tf = Tf;
+    w.T = T;
+    return true;
   }
 }
 
 template <typename TS, int CMP>
-__global__ void __launch_bounds__(kNT, kCtasPerSm) k_batched(const BatchParams p) {
+__global__ void __launch_bounds__(kNT, kCtasPerSm) k_batched_select(const Params p) {
   __shared__ uint32_t s_scr[kWarps * 64];
+  __shared__ uint32_t s_queue;
   const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lt = (1u << lane) - 1u;
   uint32_t* scr = s_scr + (threadIdx.x >> 5) * 64;
+  uint32_t q_end = 0;
+  if (p.sitems) {
+    if (threadIdx.x == 0) s_queue = p.scta[blockIdx.x];
+    q_end = p.scta[blockIdx.x + 1];
+  }
+  __syncthreads();
   SelCounters cnt;
-  uint32_t status_acc = 0;
+  uint32_t st_acc = 0;
+  Lane<TS> L;
+  WItem<TS> cur;
+  Claimer cl;
+  bool have = next_item<TS, CMP>(p, &s_queue, q_end, cl, cur, st_acc);
+  bool tail = false;
   for (;;) {
-    uint32_t i = 0;
-    if (lane == 0) i = atomicAdd(&p.work->queue, 1u);
-    i = __shfl_sync(kFull, i, 0);
-    if (i >= p.B) break;
-    const uint32_t b = p.order ? __ldg(p.order + i) : i;
-    int64_t v = 0;
-    if (lane < 2) v = __ldg(p.offsets + b + lane);
-    else if (lane < 4) v = __ldg(p.out_offsets + b + lane - 2);
-    const int64_t a0 = __shfl_sync(kFull, v, 0), a1 = __shfl_sync(kFull, v, 1);
-    const int64_t o0 = __shfl_sync(kFull, v, 2), o1 = __shfl_sync(kFull, v, 3);
-    const uint32_t K = o1 > o0 ? (uint32_t)(o1 - o0) : 0u;
-    int32_t* idx = p.idx + o0;
-    uint32_t st = 0;
-    uint32_t M = 0;
-    if (a1 < a0 || a1 - a0 >= (1ll << 31)) {
-      st = AR_STATUS_UNSUPPORTED;
-      M = a1 < a0 ? 0u : 0x7fffffffu;
+    // ---- refill idle lanes from the current item (claiming the next one
+    // when it runs out); in the tail the remaining selections share lanes
+    if (!tail) {
+      uint32_t idle = __ballot_sync(kFull, !L.act);
+      while (idle && have) {
+        const uint32_t avail = cur.s1 - cur.s;
+        const uint32_t rank = __popc(idle & lt);
+        if (!L.act && rank < avail) {
+          L.act = true;
+          L.sel = cur.s + rank;
+          L.cnt = 0;
+          L.M = cur.M;
+          L.b = cur.b;
+          L.a = cur.a;
+          L.out = cur.out;
+          L.Tf = cur.Tf;
+          L.T = cur.T;
+        }
+        const uint32_t ni = __popc(idle);
+        cur.s += ni < avail ? ni : avail;
+        if (cur.s == cur.s1) have = next_item<TS, CMP>(p, &s_queue, q_end, cl, cur, st_acc);
+        idle = __ballot_sync(kFull, !L.act);
+      }
+    }
+    const uint32_t act_mask = __ballot_sync(kFull, L.act);
+    if (!act_mask) break;
+    const uint32_t nA = __popc(act_mask);
+    if (!have && !tail && nA < 16) tail = true;
+    if (!tail) {
+      // ---- steady round: U Philox blocks of the lane's own selection
+      if (L.act) {
+        uint32_t jh = 0;
+        const unsigned long long base = 2ull * L.cnt;
+        const unsigned long long left = p.cap - base;
+        const uint32_t nvalid = left < 2 * kU ? (uint32_t)left : 2u * kU;
+        const int hit =
+            eval_blocks<TS, CMP>(p, L.cnt, L.sel, L.b, L.M, L.a, L.Tf, L.T, nvalid, jh);
+        if (hit >= 0) {
+          L.out[L.sel] = (int32_t)jh;
+          cnt.trials += base + (unsigned long long)hit + 1ull;
+          cnt.accepted += 1;
+          L.act = false;
+        } else {
+          L.cnt += kU;
+          if (2ull * L.cnt >= p.cap) {
+            L.out[L.sel] = (int32_t)L.M;
+            cnt.trials += p.cap;
+            cnt.capped += 1;
+            L.act = false;
+          }
+        }
+      }
     } else {
-      M = (uint32_t)(a1 - a0);
-    }
-    const TS* a = reinterpret_cast<const TS*>(p.alpha) + a0;
-    double T = 0.0, sum = 0.0;
-    if (!st) {
-      bool bad = false;
-      warp_bound<TS>(a, M, T, sum, bad);
-      if (bad) st = AR_STATUS_BAD_ALPHA;
-      else if (T == 0.0) st = AR_STATUS_ALL_ZERO;
-      else if (CMP == AR_CMP_F32 && isinf(__double2float_rn(T))) st = AR_STATUS_BAD_BOUND;
-    }
-    if (lane == 0) {
-      double* o = p.bound_sum + 2 * (size_t)b;
-      o[0] = T;
-      o[1] = sum;
-    }
-    if (st) {
-      status_acc |= st;
-      warp_fill(0, K, (int32_t)M, idx);
-      continue;
-    }
-    const uint32_t bid = p.b_base + b;
-    if constexpr (CMP == AR_CMP_F32) {
-      const float Tf = __double2float_rn(T);
-      auto acc = [&](uint32_t j, uint32_t w) -> bool {
-        float x;
-        if constexpr (sizeof(TS) == 4) x = __ldg(a + j);
-        else x = __double2float_rn(__ldg(a + j));
-        return accept_f32(w, Tf, x);
-      };
-      warp_select(0u, K, p.sel_base, M, bid, p.k0, p.k1, p.cap, acc, idx, scr, cnt);
-    } else {
-      auto acc = [&](uint32_t j, uint32_t w) -> bool {
-        return accept_f64(w, T, (double)__ldg(a + j));
-      };
-      warp_select(0u, K, p.sel_base, M, bid, p.k0, p.k1, p.cap, acc, idx, scr, cnt);
+      // ---- tail round: compact the active selections into lanes [0, nA)
+      if (act_mask != (nA == 32 ? kFull : (1u << nA) - 1u)) {
+        if (L.act) scr[__popc(act_mask & lt)] = lane;
+        __syncwarp();
+        const uint32_t from = lane < nA ? scr[lane] : lane;
+        __syncwarp();
+        const uint32_t sel2 = __shfl_sync(kFull, L.sel, from);
+        const uint32_t cnt2 = __shfl_sync(kFull, L.cnt, from);
+        const uint32_t M2 = __shfl_sync(kFull, L.M, from);
+        const uint32_t b2 = __shfl_sync(kFull, L.b, from);
+        const TS* a2 =
+            reinterpret_cast<const TS*>(__shfl_sync(kFull, (unsigned long long)L.a, from));
+        int32_t* o2 =
+            reinterpret_cast<int32_t*>(__shfl_sync(kFull, (unsigned long long)L.out, from));
+        const float Tf2 = __shfl_sync(kFull, L.Tf, from);
+        const double T2 = __shfl_sync(kFull, L.T, from);
+        L.act = lane < nA;
+        L.sel = sel2;
+        L.cnt = cnt2;
+        L.M = M2;
+        L.b = b2;
+        L.a = a2;
+        L.out = o2;
+        L.Tf = Tf2;
+        L.T = T2;
+      }
+      // G = 32 >> ceil(log2 nA) lanes per selection, U blocks per lane
+      const uint32_t lg = 5u - (32u - __clz(nA - 1u));
+      const uint32_t owner = lane >> lg;
+      const uint32_t g = lane & ((1u << lg) - 1u);
+      const bool valid = owner < nA;
+      const uint32_t src = owner & 31u;
+      const uint32_t o_sel = __shfl_sync(kFull, L.sel, src);
+      const uint32_t o_cnt = __shfl_sync(kFull, L.cnt, src) + g * kU;
+      const uint32_t o_M = __shfl_sync(kFull, L.M, src);
+      const uint32_t o_b = __shfl_sync(kFull, L.b, src);
+      const float o_Tf = __shfl_sync(kFull, L.Tf, src);
+      const double o_T = __shfl_sync(kFull, L.T, src);
+      const TS* o_a =
+          reinterpret_cast<const TS*>(__shfl_sync(kFull, (unsigned long long)L.a, src));
+      int hit = -1;
+      uint32_t jh = 0;
+      if (valid) {
+        const unsigned long long base = 2ull * o_cnt;
+        const unsigned long long left = base < p.cap ? p.cap - base : 0ull;
+        const uint32_t nvalid = left < 2 * kU ? (uint32_t)left : 2u * kU;
+        hit = eval_blocks<TS, CMP>(p, o_cnt, o_sel, o_b, o_M, o_a, o_Tf, o_T, nvalid, jh);
+      }
+      const uint32_t bal = __ballot_sync(kFull, hit >= 0);
+      const uint32_t seg_lo = (lane << lg) & 31u;
+      const uint32_t seg_mask = lg == 5u ? kFull : ((1u << (1u << lg)) - 1u);
+      const uint32_t seg = (bal >> seg_lo) & seg_mask;
+      const uint32_t srcl = seg_lo + (uint32_t)(__ffs(seg) - 1);
+      const uint32_t got_j = __shfl_sync(kFull, jh, srcl & 31u);
+      const uint32_t got_h = (uint32_t)__shfl_sync(kFull, hit, srcl & 31u);
+      if (L.act) {
+        if (seg) {
+          // trial index 2(cnt + g U) + hit
+          const unsigned long long t_acc =
+              2ull * (L.cnt + (srcl - seg_lo) * kU) + (unsigned long long)got_h;
+          L.out[L.sel] = (int32_t)got_j;
+          cnt.trials += t_acc + 1ull;
+          cnt.accepted += 1;
+          L.act = false;
+        } else {
+          L.cnt += (1u << lg) * kU;
+          if (2ull * L.cnt >= p.cap) {
+            L.out[L.sel] = (int32_t)L.M;
+            cnt.trials += p.cap;
+            cnt.capped += 1;
+            L.act = false;
+          }
+        }
+      }
     }
   }
-  if (cnt.capped) status_acc |= AR_STATUS_TRIAL_CAP;
+  if (cnt.capped) st_acc |= AR_STATUS_TRIAL_CAP;
   flush_counters(cnt, p.stats);
-  status_acc = __reduce_or_sync(kFull, status_acc);
-  if (lane == 0 && status_acc) atomicOr(p.status, status_acc);
+  st_acc = __reduce_or_sync(kFull, st_acc);
+  if (lane == 0 && st_acc) atomicOr(p.status, st_acc);
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    if (atomicAdd(&p.work->done, 1u) == gridDim.x - 1u) {
+    if (atomicAdd(&p.scratch->sdone, 1u) == gridDim.x - 1u) {
       // every CTA has left the claim loop: return the queue to zero
-      p.work->queue = 0u;
-      p.work->done = 0u;
+      p.scratch->squeue = 0u;
+      p.scratch->sdone = 0u;
       __threadfence();
     }
   }
 }
 
 template <typename TS, int CMP>
-int launch(const BatchParams& p, cudaStream_t s) {
-  auto kern = k_batched<TS, CMP>;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNT, 0);
-  if (per_sm < 1) per_sm = 1;
+int launch(const Params& p, bool stream_path, uint32_t sel_grid, cudaStream_t s) {
   const DeviceInfo& d = device_info();
-  const uint64_t sms = (uint64_t)(d.sm_count > 0 ? d.sm_count : 1);
-  // no more CTAs than needed to give every realization its own warp
-  const uint64_t need = ((uint64_t)p.B + kWarps - 1) / kWarps;
-  const unsigned grid = (unsigned)std::min<uint64_t>(sms * (uint64_t)per_sm, need);
-  kern<<<grid, kNT, 0, s>>>(p);
+  const uint32_t sms = (uint32_t)(d.sm_count > 0 ? d.sm_count : 1);
+  const uint32_t nitems = p.ritems ? p.nr : p.B;
+  const uint32_t need = (nitems + kBWarps - 1) / kBWarps;
+  if (stream_path) {  // plan + 16-byte aligned FP32 data
+    const uint32_t grid = std::max(1u, std::min(sms * (uint32_t)kBCtasPerSm, need));
+    k_bound_reg<<<grid, kBNT, 0, s>>>(p);
+  } else {
+    const uint32_t grid = std::max(1u, std::min(sms * 8u, need));
+    k_batched_bound<TS><<<grid, kBNT, 0, s>>>(p);
+  }
+  int rc = check_launch();
+  if (rc) return rc;
+  const uint32_t cgrid = std::max(1u, std::min(sms * 8u, (p.B + kBWarps - 1) / kBWarps));
+  k_batched_combine<TS><<<cgrid, kBNT, 0, s>>>(p);
+  rc = check_launch();
+  if (rc) return rc;
+  k_batched_select<TS, CMP><<<sel_grid ? sel_grid : sms * kCtasPerSm, kNT, 0, s>>>(p);
   return check_launch();
 }
 
@@ -222,43 +947,142 @@ int launch(const BatchParams& p, cudaStream_t s) {
 
 using namespace gbar;
 
-// The processing order of a batch: realizations sorted by an estimate of
-// their cost, largest first, so that the work still unclaimed near the end
-// of a launch is the cheapest (longest-processing-time-first list
-// scheduling over the persistent warps).
+// ---------------------------------------------------------------------------
+// Plan: the work items of the kernels, built on the host from the offsets
+// ---------------------------------------------------------------------------
 struct ar_plan {
   int device;
   int64_t B;
-  uint32_t* d_order;
+  uint32_t nr, ns, grid, gq0;
+  RItem* d_ritems;
+  RInfo* d_rinfo;
+  SItem* d_sitems;
+  uint32_t* d_scta;
+  unsigned char* d_scratch;  // Scratch | parts[NR]
 };
 
 extern "C" int ar_plan_create(const int64_t* h_offsets, const int64_t* h_out_offsets, int64_t B,
                               ar_plan** out) {
   if (!out || B <= 0 || B >= (1ll << 31) || !h_offsets || !h_out_offsets) return AR_ERR_ARG;
   *out = nullptr;
-  // cost model: one streaming pass over M_b plus K_b selections whose trial
-  // count grows like log M_b for spread-out propensities
+  const DeviceInfo& dev = device_info();
+  const uint32_t grid = (uint32_t)std::max(1, dev.sm_count) * kCtasPerSm;
   std::vector<double> cost(B);
+  double total_cost = 0.0;
   for (int64_t b = 0; b < B; ++b) {
     const int64_t M = h_offsets[b + 1] - h_offsets[b];
     const int64_t K = h_out_offsets[b + 1] - h_out_offsets[b];
-    if (M < 0 || K < 0) return AR_ERR_ARG;
-    cost[b] = 0.4 * (double)M + 1.7 * (double)K * (0.6 + std::log((double)std::max<int64_t>(M, 2)));
+    if (M < 0 || K < 0 || M >= (1ll << 31) || K >= (1ll << 32)) return AR_ERR_ARG;
+    // selections whose expected trial count grows like log M for spread-out
+    // propensities, plus the first touch of the realization's lines
+    cost[b] = (double)K * (0.6 + std::log((double)std::max<int64_t>(M, 2))) + 0.05 * (double)M;
+    total_cost += cost[b];
   }
-  std::vector<uint32_t> order(B);
-  std::iota(order.begin(), order.end(), 0u);
+  // reduction chunks: each realization cut into ceil(M / 1024) chunks of
+  // equal length (a multiple of 4, so that only the realization's own ends
+  // are unaligned), in order
+  std::vector<RItem> ritems;
+  std::vector<RInfo> rinfo(B);
+  for (int64_t b = 0; b < B; ++b) {
+    const int64_t a0 = h_offsets[b], a1 = h_offsets[b + 1];
+    rinfo[b].p0 = (uint32_t)ritems.size();
+    const int64_t nc = std::max<int64_t>(1, (a1 - a0 + kChunk - 1) / kChunk);
+    const int64_t step = (((a1 - a0 + nc - 1) / nc) + 3) & ~int64_t(3);
+    int64_t e = a0;
+    do {
+      const int64_t nxt = std::min(a1, e + step);
+      RItem r{};
+      r.e0 = e;
+      r.n = (uint32_t)(nxt - e);
+      ritems.push_back(r);
+      e = nxt;
+    } while (e < a1);
+    rinfo[b].nch = (uint32_t)ritems.size() - rinfo[b].p0;
+    if (ritems.size() >= (1ull << 31)) return AR_ERR_ARG;
+  }
+  // Realizations by decreasing cost: the costliest go to home lists, longest
+  // processing time first onto the least loaded CTA, until the cost left is
+  // kGlobalShare of the total; the rest form the global queue in that order.
+  std::vector<int64_t> order(B);
+  std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
-                   [&](uint32_t x, uint32_t y) { return cost[x] > cost[y]; });
+                   [&](int64_t x, int64_t y) { return cost[x] > cost[y]; });
+  using Load = std::pair<double, uint32_t>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (uint32_t c = 0; c < grid; ++c) heap.push({0.0, c});
+  std::vector<std::vector<int64_t>> lists(grid);
+  double left = total_cost;
+  size_t n_home = 0;
+  for (; n_home < order.size() && left > kGlobalShare * total_cost; ++n_home) {
+    const int64_t b = order[n_home];
+    Load l = heap.top();
+    heap.pop();
+    lists[l.second].push_back(b);
+    l.first += cost[b];
+    heap.push(l);
+    left -= cost[b];
+  }
+  std::vector<SItem> sitems;
+  auto add_items = [&](int64_t b, uint32_t per) {
+    const uint32_t K = (uint32_t)(h_out_offsets[b + 1] - h_out_offsets[b]);
+    uint32_t s0 = 0;
+    do {  // one item even when K = 0
+      SItem s{};
+      s.a0 = h_offsets[b];
+      s.o0 = h_out_offsets[b];
+      s.M = (uint32_t)(h_offsets[b + 1] - h_offsets[b]);
+      s.b = (uint32_t)b;
+      s.s0 = s0;
+      s.s1 = (uint32_t)std::min<uint64_t>(K, (uint64_t)s0 + per);
+      sitems.push_back(s);
+      s0 = s.s1;
+    } while (s0 < K);
+  };
+  std::vector<uint32_t> scta(grid + 1, 0);
+  for (uint32_t c = 0; c < grid; ++c) {
+    for (int64_t b : lists[c]) add_items(b, kSItem);
+    scta[c + 1] = (uint32_t)sitems.size();
+  }
+  const uint32_t gq0 = (uint32_t)sitems.size();
+  for (size_t k = n_home; k < order.size(); ++k) add_items(order[k], kGItem);
+  if (sitems.size() >= (1ull << 31)) return AR_ERR_ARG;
   auto* p = new ar_plan();
-  p->device = device_info().device;
+  p->device = dev.device;
   p->B = B;
-  p->d_order = nullptr;
-  cudaError_t e = cudaMalloc(&p->d_order, sizeof(uint32_t) * (size_t)B);
+  p->nr = (uint32_t)ritems.size();
+  p->ns = (uint32_t)sitems.size();
+  p->grid = grid;
+  p->gq0 = gq0;
+  p->d_ritems = nullptr;
+  p->d_rinfo = nullptr;
+  p->d_sitems = nullptr;
+  p->d_scta = nullptr;
+  p->d_scratch = nullptr;
+  const size_t scratch_bytes = sizeof(Scratch) + sizeof(Part) * ritems.size();
+  cudaError_t e = cudaMalloc(&p->d_ritems, sizeof(RItem) * ritems.size());
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_rinfo, sizeof(RInfo) * rinfo.size());
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_sitems, sizeof(SItem) * sitems.size());
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_scta, sizeof(uint32_t) * scta.size());
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_scratch, scratch_bytes);
   if (e == cudaSuccess)
-    e = cudaMemcpy(p->d_order, order.data(), sizeof(uint32_t) * (size_t)B, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(p->d_ritems, ritems.data(), sizeof(RItem) * ritems.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_rinfo, rinfo.data(), sizeof(RInfo) * rinfo.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_sitems, sitems.data(), sizeof(SItem) * sitems.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_scta, scta.data(), sizeof(uint32_t) * scta.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(p->d_scratch, 0, sizeof(Scratch));
   if (e != cudaSuccess) {
     set_cuda_error(e);
-    cudaFree(p->d_order);
+    cudaFree(p->d_ritems);
+    cudaFree(p->d_rinfo);
+    cudaFree(p->d_sitems);
+    cudaFree(p->d_scta);
+    cudaFree(p->d_scratch);
     delete p;
     return AR_ERR_CUDA;
   }
@@ -271,14 +1095,18 @@ extern "C" void ar_plan_destroy(ar_plan* plan) {
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != plan->device) cudaSetDevice(plan->device);
-  cudaFree(plan->d_order);
+  cudaFree(plan->d_ritems);
+  cudaFree(plan->d_rinfo);
+  cudaFree(plan->d_sitems);
+  cudaFree(plan->d_scta);
+  cudaFree(plan->d_scratch);
   if (cur != plan->device) cudaSetDevice(cur);
   delete plan;
 }
 
 extern "C" size_t ar_select_batched_workspace_size(int64_t B) {
-  (void)B;
-  return sizeof(BatchWork);
+  if (B < 0 || B >= (1ll << 31)) return 0;
+  return sizeof(Scratch) + sizeof(Part) * (size_t)B;
 }
 
 extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64_t* d_offsets,
@@ -296,18 +1124,33 @@ extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64
       !aligned(d_out_offsets, 8) || !aligned(d_bound_sum, 8) || !aligned(d_idx, 4) ||
       !aligned(d_status, 4) || !aligned(d_stats, 8))
     return AR_ERR_ALIGN;
-  if (!d_work || work_bytes < ar_select_batched_workspace_size(B)) return AR_ERR_WORKSPACE;
-  if (!aligned(d_work, 16)) return AR_ERR_ALIGN;
   if ((uint64_t)realization_base + (uint64_t)B > (1ull << 32)) return AR_ERR_ARG;
   if (sel_offset >= (1ull << 32)) return AR_ERR_ARG;
+  Params p{};
+  uint32_t sel_grid = 0;
+  p.vec_ok = aligned(d_alpha_cat, 16) ? 1u : 0u;
+  bool stream_path = false;
   if (plan) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (plan->B != B || plan->device != dev) return AR_ERR_ARG;
+    p.ritems = plan->d_ritems;
+    p.rinfo = plan->d_rinfo;
+    p.sitems = plan->d_sitems;
+    p.scta = plan->d_scta;
+    p.nr = plan->nr;
+    p.gq0 = plan->gq0;
+    p.gq1 = plan->ns;
+    p.scratch = reinterpret_cast<Scratch*>(plan->d_scratch);
+    p.parts = reinterpret_cast<Part*>(plan->d_scratch + sizeof(Scratch));
+    sel_grid = plan->grid;
+    stream_path = dtype == AR_F32 && p.vec_ok;
+  } else {
+    if (!d_work || work_bytes < ar_select_batched_workspace_size(B)) return AR_ERR_WORKSPACE;
+    if (!aligned(d_work, 16)) return AR_ERR_ALIGN;
+    p.scratch = static_cast<Scratch*>(d_work);
+    p.parts = reinterpret_cast<Part*>(static_cast<unsigned char*>(d_work) + sizeof(Scratch));
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  BatchParams p{};
-  p.order = plan ? plan->d_order : nullptr;
   p.alpha = static_cast<const unsigned char*>(d_alpha_cat);
   p.offsets = d_offsets;
   p.out_offsets = d_out_offsets;
@@ -315,14 +1158,16 @@ extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64
   p.idx = d_idx;
   p.stats = d_stats;
   p.status = d_status;
-  p.work = static_cast<BatchWork*>(d_work);
   p.cap = trial_cap;
   p.B = (uint32_t)B;
   p.sel_base = (uint32_t)sel_offset;
   p.b_base = realization_base;
   p.k0 = (uint32_t)(seed & 0xffffffffu);
   p.k1 = (uint32_t)(seed >> 32);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (dtype == AR_F32)
-    return cmp == AR_CMP_F32 ? launch<float, AR_CMP_F32>(p, s) : launch<float, AR_CMP_F64>(p, s);
-  return cmp == AR_CMP_F32 ? launch<double, AR_CMP_F32>(p, s) : launch<double, AR_CMP_F64>(p, s);
+    return cmp == AR_CMP_F32 ? launch<float, AR_CMP_F32>(p, stream_path, sel_grid, s)
+                             : launch<float, AR_CMP_F64>(p, stream_path, sel_grid, s);
+  return cmp == AR_CMP_F32 ? launch<double, AR_CMP_F32>(p, stream_path, sel_grid, s)
+                           : launch<double, AR_CMP_F64>(p, stream_path, sel_grid, s);
 }

@@ -181,6 +181,22 @@ def test_batched_ragged(gb, orc, cmp, dtype, plan):
 
 
 @pytest.mark.parametrize("plan", [False, True])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_batched_wide_range(gb, orc, dtype, plan):
+    """Propensities spread over many binades, subnormal and -0 entries: the
+    exact fixed-point totals take every window (and drop nothing that
+    matters), the maxima stay exact."""
+    rng = np.random.default_rng(77)
+    pw = np.ldexp(1.0, rng.integers(-149, 31, size=3000)) * rng.uniform(1, 2, size=3000)
+    pw[rng.integers(0, 3000, size=50)] = -0.0
+    pw[rng.integers(0, 3000, size=50)] = 0.0
+    vecs = [W.wide_range(5000, seed=1).astype(dtype), pw.astype(np.float32).astype(dtype),
+            W.wide_range(1030, seed=2).astype(dtype), W.wide_range(70_000, seed=3).astype(dtype)]
+    _check_batched(gb, orc, W.batch_from_vectors(vecs, [100, 300, 7, 50]), cmp=0, seed=3,
+                   plan=plan)
+
+
+@pytest.mark.parametrize("plan", [False, True])
 @pytest.mark.parametrize("cmp", [0, 1])
 def test_batched_uneven_small(gb, orc, cmp, plan):
     _check_batched(gb, orc, W.batched_uneven(B=300, seed=301, K=256), cmp=cmp, plan=plan)
@@ -196,11 +212,13 @@ def test_batched_uneven_full(gb, orc, seed, plan):
 
 def test_batched_repeated_launches_reuse_workspace(gb, orc):
     """Back-to-back launches on one workspace (the benchmark's pattern, also
-    under graph replay) give identical results: the queue returns to zero."""
+    under graph replay) give identical results: the claim counter in the
+    workspace's first 16 bytes returns to zero."""
     import torch
     bt = W.batched_uneven(B=1000, seed=302, K=64)
     a, off, oo = _t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets)
-    work = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    work = torch.zeros(gb.ar_select_batched_workspace_size(bt.B), dtype=torch.uint8,
+                       device="cuda")
     bs = torch.empty((bt.B, 2), dtype=torch.float64, device="cuda")
     idx = torch.empty(int(bt.out_offsets[-1]), dtype=torch.int32, device="cuda")
     stats = torch.zeros(3, dtype=torch.int64, device="cuda")
@@ -224,5 +242,5 @@ def test_batched_repeated_launches_reuse_workspace(gb, orc):
                 g.replay()
                 s.synchronize()
                 assert np.array_equal(idx.cpu().numpy(), oidx)
-        assert work.cpu().numpy().tolist() == [0] * 16
+        assert work[:16].cpu().numpy().tolist() == [0] * 16
     assert int(st.item()) == 0
