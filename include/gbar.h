@@ -161,10 +161,11 @@ int ar_select_k(const void *d_alpha, int dtype, int64_t M, const double *d_bound
                 uint32_t *d_status, void *stream);
 
 /* ---------------------------------------------------------------------
- * ar_select_batched -- many realizations with uneven M_b and K_b in two
- * persistent launches enqueued on the stream, a chunked reduction and the
- * selections (Section "A GPU acceptance-rejection algorithm": K
- * realizations as K blocks; the text's extension to M beyond one block).
+ * ar_select_batched -- many realizations with uneven M_b and K_b:
+ * ar_bound_batched followed by ar_select_batched_bounded with each
+ * realization's own maximum as its bound (three kernels enqueued on the
+ * stream; Section "A GPU acceptance-rejection algorithm": K realizations as
+ * K blocks; the text's extension to M beyond one block).
  * Realization b owns alpha_cat[offsets[b] .. offsets[b+1]) and writes
  * K_b = out_offsets[b+1] - out_offsets[b] indices at d_idx[out_offsets[b]].
  * Its bound is its own maximum, computed in the kernel; its Philox
@@ -192,10 +193,46 @@ int ar_select_k(const void *d_alpha, int dtype, int64_t M, const double *d_bound
  *                    rewritten by every call.  Calls sharing a workspace must
  *                    not overlap.
  *   d_idx, d_stats, d_status   as in ar_select_k (status also collects
- *                    BAD_ALPHA and ALL_ZERO of any realization).
+ *                    BAD_ALPHA and ALL_ZERO of any realization).  An
+ *                    invalid realization (BAD_ALPHA) gets no selections:
+ *                    its indices are the sentinel M_b.
  * ------------------------------------------------------------------- */
 typedef struct ar_plan ar_plan;
 size_t ar_select_batched_workspace_size(int64_t B);
+
+/* ---------------------------------------------------------------------
+ * ar_bound_batched -- the reduction step alone (Section "A GPU
+ * acceptance-rejection algorithm": T = max_j alpha_j per realization; the
+ * total alpha_0 = sum_j alpha_j of Section "The Stochastic Simulation
+ * Algorithm").  Arguments as in ar_select_batched; d_bound_sum [B][2]
+ * receives {max, sum} (NaN, NaN for an invalid realization).  d_status
+ * collects BAD_ALPHA, UNSUPPORTED and ALL_ZERO (a valid realization whose
+ * propensities are all zero, including M_b = 0).  Two kernels.
+ * ------------------------------------------------------------------- */
+int ar_bound_batched(const void *d_alpha_cat, int dtype, const int64_t *d_offsets, int64_t B,
+                     const struct ar_plan *plan, double *d_bound_sum, uint32_t *d_status,
+                     void *d_work, size_t work_bytes, void *stream);
+
+/* ---------------------------------------------------------------------
+ * ar_select_batched_bounded -- the selection step with the caller's bounds:
+ * realization b uses T_b = d_bound[b * bound_stride] (bound_stride = 2
+ * reads the maxima of a bound_sum array).  The paper's threshold
+ * experiment T_w = w * max_j alpha_j (Section "Test and validation"):
+ * any T_b >= max_j alpha_j keeps the law exact and lowers the acceptance
+ * rate by the factor max / T_b; a T_b below the maximum biases the law
+ * (not checked).  Per realization, as ar_select_k with d_bound: T_b NaN,
+ * negative or infinite (or infinite in FP32 with AR_CMP_F32) raises
+ * BAD_BOUND and gives the sentinel M_b; T_b = 0 or M_b = 0 raises ALL_ZERO
+ * (when K_b > 0) and gives M_b.  Other arguments as in ar_select_batched.
+ * One kernel.
+ * ------------------------------------------------------------------- */
+int ar_select_batched_bounded(const void *d_alpha_cat, int dtype, const int64_t *d_offsets,
+                              const int64_t *d_out_offsets, int64_t B, const double *d_bound,
+                              int64_t bound_stride, uint64_t seed, uint64_t sel_offset,
+                              uint32_t realization_base, int cmp, uint64_t trial_cap,
+                              const struct ar_plan *plan, int32_t *d_idx, ar_stats *d_stats,
+                              uint32_t *d_status, void *d_work, size_t work_bytes,
+                              void *stream);
 
 /* ---------------------------------------------------------------------
  * ar_plan_create -- tuning handle for repeated ar_select_batched calls on

@@ -62,6 +62,9 @@ def lib():
         L.orc_select_batched.argtypes = [vp, i32, vp, vp, i64, u64, u64, u32, i32, u64,
                                          vp, vp, vp, i32]
         L.orc_select_batched.restype = u32
+        L.orc_select_batched_bounded.argtypes = [vp, i32, vp, vp, i64, vp, i64, u64, u64, u32,
+                                                 i32, u64, vp, vp, i32]
+        L.orc_select_batched_bounded.restype = u32
         L.orc_select_it.argtypes = [vp, i32, i64, i64, u64, u64, u32, vp, i32]
         L.orc_select_it.restype = u32
         L.orc_select_paper.argtypes = [vp, i64, ctypes.c_float, i64, u64, u64, u32, vp, vp, i32]
@@ -134,6 +137,25 @@ def select_batched(batch, seed=1, sel_offset=0, realization_base=0, cmp=CMP_F32,
                                   realization_base, cmp, ctypes.c_uint64(trial_cap),
                                   _ptr(bs), _ptr(idx), _ptr(stats), nthreads)
     return bs, idx, stats, int(st)
+
+
+def select_batched_bounded(batch, bound, stride=1, seed=1, sel_offset=0, realization_base=0,
+                           cmp=CMP_F32, trial_cap=1 << 20, nthreads=1):
+    """Batched selection with the caller's bounds T_b = bound[b * stride]
+    -> (idx int32[sum K], stats uint64[3], status)."""
+    a = np.ascontiguousarray(batch.alpha)
+    off = np.ascontiguousarray(batch.offsets, dtype=np.int64)
+    oo = np.ascontiguousarray(batch.out_offsets, dtype=np.int64)
+    bd = np.ascontiguousarray(bound, dtype=np.float64)
+    B = len(off) - 1
+    idx = np.zeros(int(oo[-1]), dtype=np.int32)
+    stats = np.zeros(3, dtype=np.uint64)
+    st = lib().orc_select_batched_bounded(_ptr(a), _dtype_code(a), _ptr(off), _ptr(oo), B,
+                                          _ptr(bd), stride, ctypes.c_uint64(seed),
+                                          ctypes.c_uint64(sel_offset), realization_base, cmp,
+                                          ctypes.c_uint64(trial_cap), _ptr(idx), _ptr(stats),
+                                          nthreads)
+    return idx, stats, int(st)
 
 
 def select_it(alpha, K, seed=1, sel_offset=0, realization=0, nthreads=1):

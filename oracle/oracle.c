@@ -235,9 +235,16 @@ uint32_t orc_select_batched(const void *alpha, int dtype, const int64_t *offsets
         int64_t Kb = out_offsets[b + 1] - out_offsets[b];
         double bs[2];
         uint32_t sb = orc_bound(ab, dtype, Mb, bs);
+        if (sb & ST_BAD_ALPHA) {
+            /* an invalid realization has no usable bound: (NaN, NaN), no
+             * selections (every index is the sentinel M) */
+            bound_sum[2 * b] = bound_sum[2 * b + 1] = NAN;
+            for (int64_t i = 0; i < Kb; i++) idx[out_offsets[b] + i] = (int32_t)Mb;
+            status |= ST_BAD_ALPHA;
+            continue;
+        }
         bound_sum[2 * b] = bs[0];
         bound_sum[2 * b + 1] = bs[1];
-        status |= sb & ST_BAD_ALPHA;
         status |= orc_select_ar(ab, dtype, Mb, bs[0], Kb, seed, sel_offset,
                                 realization_base + (uint32_t)b, cmp, trial_cap,
                                 idx + out_offsets[b], st, nthreads);
@@ -246,6 +253,27 @@ uint32_t orc_select_batched(const void *alpha, int dtype, const int64_t *offsets
         stats[0] += st[0];
         stats[1] += st[1];
         stats[2] += st[2];
+    }
+    return status;
+}
+
+/* Batched selection with the caller's bounds: realization b uses
+ * T_b = bound[b * stride] (T_w = w * max_j alpha_j, the paper's threshold
+ * experiment, keeps the law for w >= 1).  Each realization as orc_select_ar. */
+uint32_t orc_select_batched_bounded(const void *alpha, int dtype, const int64_t *offsets,
+                                    const int64_t *out_offsets, int64_t B, const double *bound,
+                                    int64_t stride, uint64_t seed, uint64_t sel_offset,
+                                    uint32_t realization_base, int cmp, uint64_t trial_cap,
+                                    int32_t *idx, uint64_t stats[3], int nthreads)
+{
+    uint32_t status = 0;
+    int64_t esize = dtype == 0 ? 4 : 8;
+    for (int64_t b = 0; b < B; b++) {
+        const char *ab = (const char *)alpha + offsets[b] * esize;
+        status |= orc_select_ar(ab, dtype, offsets[b + 1] - offsets[b], bound[b * stride],
+                                out_offsets[b + 1] - out_offsets[b], seed, sel_offset,
+                                realization_base + (uint32_t)b, cmp, trial_cap,
+                                idx + out_offsets[b], stats, nthreads);
     }
     return status;
 }

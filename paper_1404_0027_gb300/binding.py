@@ -65,6 +65,9 @@ SIGNATURES = {
     "ar_plan_destroy": (None, [_vp]),
     "ar_select_batched": (_int, [_vp, _int, _vp, _vp, _i64, _u64, _u64, _u32, _int, _u64, _vp,
                                  _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "ar_bound_batched": (_int, [_vp, _int, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "ar_select_batched_bounded": (_int, [_vp, _int, _vp, _vp, _i64, _vp, _i64, _u64, _u64, _u32,
+                                         _int, _u64, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
 }
 
 
@@ -209,10 +212,39 @@ def ar_select_batched(alpha_cat, offsets, out_offsets, seed, sel_offset, realiza
         _dev(alpha_cat, name="alpha_cat"), _dtype_code(alpha_cat),
         _dev(offsets, torch.int64, "offsets"), _dev(out_offsets, torch.int64, "out_offsets"), B,
         seed, sel_offset, realization_base, cmp, trial_cap,
-        None if plan is None else ctypes.c_void_p(plan.handle if isinstance(plan, Plan) else plan),
-        _dev(bound_sum, torch.float64, "bound_sum"), _dev(idx, torch.int32, "idx"),
+        _plan_ptr(plan), _dev(bound_sum, torch.float64, "bound_sum"), _dev(idx, torch.int32, "idx"),
         _dev(stats, torch.int64, "stats"), _dev(status, torch.int32, "status"),
         _dev(work, name="work"), nbytes, _stream(stream)), "ar_select_batched")
+
+
+def _plan_ptr(plan):
+    if plan is None:
+        return None
+    return ctypes.c_void_p(plan.handle if isinstance(plan, Plan) else plan)
+
+
+def ar_bound_batched(alpha_cat, offsets, plan, bound_sum, status, work, stream=None):
+    B = offsets.numel() - 1
+    nbytes = 0 if work is None else work.numel() * work.element_size()
+    _check(lib().ar_bound_batched(
+        _dev(alpha_cat, name="alpha_cat"), _dtype_code(alpha_cat),
+        _dev(offsets, torch.int64, "offsets"), B, _plan_ptr(plan),
+        _dev(bound_sum, torch.float64, "bound_sum"), _dev(status, torch.int32, "status"),
+        _dev(work, name="work"), nbytes, _stream(stream)), "ar_bound_batched")
+
+
+def ar_select_batched_bounded(alpha_cat, offsets, out_offsets, bound, bound_stride, seed,
+                              sel_offset, realization_base, cmp, trial_cap, plan, idx, stats,
+                              status, work, stream=None):
+    B = offsets.numel() - 1
+    nbytes = 0 if work is None else work.numel() * work.element_size()
+    _check(lib().ar_select_batched_bounded(
+        _dev(alpha_cat, name="alpha_cat"), _dtype_code(alpha_cat),
+        _dev(offsets, torch.int64, "offsets"), _dev(out_offsets, torch.int64, "out_offsets"), B,
+        _dev(bound, torch.float64, "bound"), bound_stride, seed, sel_offset, realization_base,
+        cmp, trial_cap, _plan_ptr(plan), _dev(idx, torch.int32, "idx"),
+        _dev(stats, torch.int64, "stats"), _dev(status, torch.int32, "status"),
+        _dev(work, name="work"), nbytes, _stream(stream)), "ar_select_batched_bounded")
 
 
 # --------------------------------------------------------------------------
@@ -255,6 +287,35 @@ def select_batched(alpha_cat, offsets, out_offsets, seed=1, sel_offset=0, realiz
     ar_select_batched(alpha_cat, offsets, out_offsets, seed, sel_offset, realization_base, cmp,
                       trial_cap, plan, bs, idx, stats, st, work, stream)
     return bs, idx, stats, st
+
+
+def bound_batched(alpha_cat, offsets, plan=None, stream=None):
+    """-> (bound_sum f64[B,2], status int32[1])."""
+    dev = alpha_cat.device
+    B = offsets.numel() - 1
+    bs = torch.empty((B, 2), dtype=torch.float64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    work = torch.zeros(max(ar_select_batched_workspace_size(B), 16), dtype=torch.uint8,
+                       device=dev)
+    ar_bound_batched(alpha_cat, offsets, plan, bs, st, work, stream)
+    return bs, st
+
+
+def select_batched_bounded(alpha_cat, offsets, out_offsets, bound, bound_stride=1, seed=1,
+                           sel_offset=0, realization_base=0, cmp=AR_CMP_F32, trial_cap=1 << 20,
+                           plan=None, stream=None):
+    """-> (idx int32[sum K], stats int64[3], status int32[1])."""
+    dev = alpha_cat.device
+    B = offsets.numel() - 1
+    idx = torch.empty(int(out_offsets[-1].item()), dtype=torch.int32, device=dev)
+    stats = torch.zeros(3, dtype=torch.int64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    work = torch.zeros(max(ar_select_batched_workspace_size(B), 16), dtype=torch.uint8,
+                       device=dev)
+    ar_select_batched_bounded(alpha_cat, offsets, out_offsets, bound, bound_stride, seed,
+                              sel_offset, realization_base, cmp, trial_cap, plan, idx, stats, st,
+                              work, stream)
+    return idx, stats, st
 
 
 # --------------------------------------------------------------------------

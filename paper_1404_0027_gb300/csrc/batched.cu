@@ -110,6 +110,11 @@ struct Params {
   uint32_t b_base;
   uint32_t k0, k1;
   uint32_t vec_ok;  // alpha_cat is 16-byte aligned (vector loads)
+  // selection bounds: T_b = bound_in[b * bound_stride]
+  const double* bound_in;
+  int64_t bound_stride;
+  uint32_t bound_given;  // caller's bounds: checked like ar_select_k's
+  uint32_t zero_status;  // the reduction reports all-zero realizations
 };
 
 // ===========================================================================
@@ -591,6 +596,7 @@ __global__ void __launch_bounds__(kBNT) k_batched_combine(const Params p) {
         o[0] = sizeof(TS) == 4 ? (double)__uint_as_float((uint32_t)vm)
                                : __longlong_as_double((long long)vm);
         o[1] = sum;
+        if (p.zero_status && vm == 0) st_acc |= AR_STATUS_ALL_ZERO;
       }
     }
   }
@@ -728,16 +734,20 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
       s0 = 0;
       s1 = o1 > o0 ? (uint32_t)(o1 - o0) : 0u;
     }
-    // the bound written by k_batched_combine (NaN: unusable realization)
-    const double T = __ldcg(p.bound_sum + 2 * (size_t)b);
-    const float Tf = sizeof(TS) == 4 ? (float)T : __double2float_rn(T);
+    // the bound: from k_batched_combine (NaN: invalid realization, already
+    // reported) or the caller's (NaN, < 0 or infinite: BAD_BOUND)
+    const double T = __ldcg(p.bound_in + (size_t)b * (size_t)p.bound_stride);
+    const float Tf = __double2float_rn(T);
     int32_t* out = p.idx + o0;
     uint32_t st = 0;
-    if (T != T) st = 1;                          // raised by k_batched_combine
-    else if (T == 0.0) st = AR_STATUS_ALL_ZERO;  // the paper's rejection case
+    if (p.bound_given && (!(T >= 0.0) || isinf(T))) st = AR_STATUS_BAD_BOUND;
+    else if (T != T) st = 1;
     else if (CMP == AR_CMP_F32 && isinf(Tf)) st = AR_STATUS_BAD_BOUND;
+    else if (T == 0.0 || M == 0) st = AR_STATUS_ALL_ZERO;  // the paper's rejection case
     if (st) {
-      if (st != 1 && s1 > s0) st_acc |= st;
+      // BAD_BOUND is reported for every realization it hits, ALL_ZERO only
+      // for realizations with selections
+      if (st == AR_STATUS_BAD_BOUND || (st == AR_STATUS_ALL_ZERO && s1 > s0)) st_acc |= st;
       for (uint32_t k = s0 + lane; k < s1; k += 32) out[k] = (int32_t)M;
       continue;
     }
@@ -919,8 +929,9 @@ __global__ void __launch_bounds__(kNT, kCtasPerSm) k_batched_select(const Params
   }
 }
 
-template <typename TS, int CMP>
-int launch(const Params& p, bool stream_path, uint32_t sel_grid, cudaStream_t s) {
+// The reduction and combine kernels (bound_sum and status).
+template <typename TS>
+int launch_bound(const Params& p, bool stream_path, cudaStream_t s) {
   const DeviceInfo& d = device_info();
   const uint32_t sms = (uint32_t)(d.sm_count > 0 ? d.sm_count : 1);
   const uint32_t nitems = p.ritems ? p.nr : p.B;
@@ -932,12 +943,18 @@ int launch(const Params& p, bool stream_path, uint32_t sel_grid, cudaStream_t s)
     const uint32_t grid = std::max(1u, std::min(sms * 8u, need));
     k_batched_bound<TS><<<grid, kBNT, 0, s>>>(p);
   }
-  int rc = check_launch();
+  const int rc = check_launch();
   if (rc) return rc;
   const uint32_t cgrid = std::max(1u, std::min(sms * 8u, (p.B + kBWarps - 1) / kBWarps));
   k_batched_combine<TS><<<cgrid, kBNT, 0, s>>>(p);
-  rc = check_launch();
-  if (rc) return rc;
+  return check_launch();
+}
+
+// The selection kernel (bounds from p.bound_in).
+template <typename TS, int CMP>
+int launch_select(const Params& p, uint32_t sel_grid, cudaStream_t s) {
+  const DeviceInfo& d = device_info();
+  const uint32_t sms = (uint32_t)(d.sm_count > 0 ? d.sm_count : 1);
   k_batched_select<TS, CMP><<<sel_grid ? sel_grid : sms * kCtasPerSm, kNT, 0, s>>>(p);
   return check_launch();
 }
@@ -1109,27 +1126,22 @@ extern "C" size_t ar_select_batched_workspace_size(int64_t B) {
   return sizeof(Scratch) + sizeof(Part) * (size_t)B;
 }
 
-extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64_t* d_offsets,
-                                 const int64_t* d_out_offsets, int64_t B, uint64_t seed,
-                                 uint64_t sel_offset, uint32_t realization_base, int cmp,
-                                 uint64_t trial_cap, const ar_plan* plan, double* d_bound_sum,
-                                 int32_t* d_idx, ar_stats* d_stats, uint32_t* d_status,
-                                 void* d_work, size_t work_bytes, void* stream) {
-  if (!valid_dtype(dtype) || !valid_cmp(cmp) || B < 0 || B >= (1ll << 31)) return AR_ERR_ARG;
-  if (trial_cap < 1 || trial_cap > (1ull << 32)) return AR_ERR_ARG;
-  if (B == 0) return AR_OK;
-  if (!d_alpha_cat || !d_offsets || !d_out_offsets || !d_bound_sum || !d_idx || !d_status)
-    return AR_ERR_ARG;
+namespace {
+
+// Argument checks and Params common to the batched entry points.
+int batched_params(const void* d_alpha_cat, int dtype, const int64_t* d_offsets,
+                   const int64_t* d_out_offsets, int64_t B, const ar_plan* plan,
+                   uint32_t* d_status, void* d_work, size_t work_bytes, Params& p,
+                   uint32_t& sel_grid, bool& stream_path) {
+  if (!valid_dtype(dtype) || B < 0 || B >= (1ll << 31)) return AR_ERR_ARG;
+  if (!d_alpha_cat || !d_offsets || !d_status) return AR_ERR_ARG;
   if (!aligned(d_alpha_cat, dtype_size(dtype)) || !aligned(d_offsets, 8) ||
-      !aligned(d_out_offsets, 8) || !aligned(d_bound_sum, 8) || !aligned(d_idx, 4) ||
-      !aligned(d_status, 4) || !aligned(d_stats, 8))
+      !aligned(d_out_offsets, 8) || !aligned(d_status, 4))
     return AR_ERR_ALIGN;
-  if ((uint64_t)realization_base + (uint64_t)B > (1ull << 32)) return AR_ERR_ARG;
-  if (sel_offset >= (1ull << 32)) return AR_ERR_ARG;
-  Params p{};
-  uint32_t sel_grid = 0;
+  p = Params{};
+  sel_grid = 0;
+  stream_path = false;
   p.vec_ok = aligned(d_alpha_cat, 16) ? 1u : 0u;
-  bool stream_path = false;
   if (plan) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -1154,20 +1166,109 @@ extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64
   p.alpha = static_cast<const unsigned char*>(d_alpha_cat);
   p.offsets = d_offsets;
   p.out_offsets = d_out_offsets;
-  p.bound_sum = d_bound_sum;
+  p.status = d_status;
+  p.B = (uint32_t)B;
+  return AR_OK;
+}
+
+int selection_params(uint64_t seed, uint64_t sel_offset, uint32_t realization_base, int cmp,
+                     uint64_t trial_cap, int64_t B, const int64_t* d_out_offsets, int32_t* d_idx,
+                     ar_stats* d_stats, Params& p) {
+  if (!valid_cmp(cmp) || trial_cap < 1 || trial_cap > (1ull << 32)) return AR_ERR_ARG;
+  if ((uint64_t)realization_base + (uint64_t)B > (1ull << 32)) return AR_ERR_ARG;
+  if (sel_offset >= (1ull << 32)) return AR_ERR_ARG;
+  if (!d_out_offsets || !d_idx) return AR_ERR_ARG;
+  if (!aligned(d_idx, 4) || !aligned(d_stats, 8)) return AR_ERR_ALIGN;
   p.idx = d_idx;
   p.stats = d_stats;
-  p.status = d_status;
   p.cap = trial_cap;
-  p.B = (uint32_t)B;
   p.sel_base = (uint32_t)sel_offset;
   p.b_base = realization_base;
   p.k0 = (uint32_t)(seed & 0xffffffffu);
   p.k1 = (uint32_t)(seed >> 32);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return AR_OK;
+}
+
+int dispatch_select(int dtype, int cmp, const Params& p, uint32_t sel_grid, cudaStream_t s) {
   if (dtype == AR_F32)
-    return cmp == AR_CMP_F32 ? launch<float, AR_CMP_F32>(p, stream_path, sel_grid, s)
-                             : launch<float, AR_CMP_F64>(p, stream_path, sel_grid, s);
-  return cmp == AR_CMP_F32 ? launch<double, AR_CMP_F32>(p, stream_path, sel_grid, s)
-                           : launch<double, AR_CMP_F64>(p, stream_path, sel_grid, s);
+    return cmp == AR_CMP_F32 ? launch_select<float, AR_CMP_F32>(p, sel_grid, s)
+                             : launch_select<float, AR_CMP_F64>(p, sel_grid, s);
+  return cmp == AR_CMP_F32 ? launch_select<double, AR_CMP_F32>(p, sel_grid, s)
+                           : launch_select<double, AR_CMP_F64>(p, sel_grid, s);
+}
+
+}  // namespace
+
+extern "C" int ar_bound_batched(const void* d_alpha_cat, int dtype, const int64_t* d_offsets,
+                                int64_t B, const ar_plan* plan, double* d_bound_sum,
+                                uint32_t* d_status, void* d_work, size_t work_bytes,
+                                void* stream) {
+  if (B == 0 && valid_dtype(dtype)) return AR_OK;
+  Params p;
+  uint32_t sel_grid;
+  bool stream_path;
+  int rc = batched_params(d_alpha_cat, dtype, d_offsets, d_offsets, B, plan, d_status, d_work,
+                          work_bytes, p, sel_grid, stream_path);
+  if (rc) return rc;
+  if (!d_bound_sum) return AR_ERR_ARG;
+  if (!aligned(d_bound_sum, 8)) return AR_ERR_ALIGN;
+  p.bound_sum = d_bound_sum;
+  p.zero_status = 1u;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return dtype == AR_F32 ? launch_bound<float>(p, stream_path, s)
+                         : launch_bound<double>(p, stream_path, s);
+}
+
+extern "C" int ar_select_batched_bounded(const void* d_alpha_cat, int dtype,
+                                         const int64_t* d_offsets, const int64_t* d_out_offsets,
+                                         int64_t B, const double* d_bound, int64_t bound_stride,
+                                         uint64_t seed, uint64_t sel_offset,
+                                         uint32_t realization_base, int cmp, uint64_t trial_cap,
+                                         const ar_plan* plan, int32_t* d_idx, ar_stats* d_stats,
+                                         uint32_t* d_status, void* d_work, size_t work_bytes,
+                                         void* stream) {
+  if (B == 0 && valid_dtype(dtype) && valid_cmp(cmp)) return AR_OK;
+  Params p;
+  uint32_t sel_grid;
+  bool stream_path;
+  int rc = batched_params(d_alpha_cat, dtype, d_offsets, d_out_offsets, B, plan, d_status,
+                          d_work, work_bytes, p, sel_grid, stream_path);
+  if (rc) return rc;
+  rc = selection_params(seed, sel_offset, realization_base, cmp, trial_cap, B, d_out_offsets,
+                        d_idx, d_stats, p);
+  if (rc) return rc;
+  if (!d_bound || bound_stride < 1) return AR_ERR_ARG;
+  if (!aligned(d_bound, 8)) return AR_ERR_ALIGN;
+  p.bound_in = d_bound;
+  p.bound_stride = bound_stride;
+  p.bound_given = 1u;
+  return dispatch_select(dtype, cmp, p, sel_grid, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64_t* d_offsets,
+                                 const int64_t* d_out_offsets, int64_t B, uint64_t seed,
+                                 uint64_t sel_offset, uint32_t realization_base, int cmp,
+                                 uint64_t trial_cap, const ar_plan* plan, double* d_bound_sum,
+                                 int32_t* d_idx, ar_stats* d_stats, uint32_t* d_status,
+                                 void* d_work, size_t work_bytes, void* stream) {
+  if (B == 0 && valid_dtype(dtype) && valid_cmp(cmp)) return AR_OK;
+  Params p;
+  uint32_t sel_grid;
+  bool stream_path;
+  int rc = batched_params(d_alpha_cat, dtype, d_offsets, d_out_offsets, B, plan, d_status,
+                          d_work, work_bytes, p, sel_grid, stream_path);
+  if (rc) return rc;
+  rc = selection_params(seed, sel_offset, realization_base, cmp, trial_cap, B, d_out_offsets,
+                        d_idx, d_stats, p);
+  if (rc) return rc;
+  if (!d_bound_sum) return AR_ERR_ARG;
+  if (!aligned(d_bound_sum, 8)) return AR_ERR_ALIGN;
+  p.bound_sum = d_bound_sum;
+  p.bound_in = d_bound_sum;
+  p.bound_stride = 2;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  rc = dtype == AR_F32 ? launch_bound<float>(p, stream_path, s)
+                       : launch_bound<double>(p, stream_path, s);
+  if (rc) return rc;
+  return dispatch_select(dtype, cmp, p, sel_grid, s);
 }

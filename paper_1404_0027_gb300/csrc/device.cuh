@@ -183,62 +183,4 @@ __device__ __forceinline__ int fx_eref(uint32_t max_bits) {
   return e < 1 ? 1 : e;
 }
 
-// ---------------------------------------------------------------------------
-// mbarrier + bulk asynchronous copy (TMA, one-dimensional form).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-// makes initialised barriers visible to the asynchronous proxy
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-// orders this thread's earlier shared-memory accesses before later
-// asynchronous-proxy (bulk copy) accesses
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// One arrival that also expects `bytes` of transaction count; with
-// bytes = 0 a plain arrival.
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
-  if (bytes)
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-  else
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-// Bulk copy global -> shared completing on `bar`: both addresses 16-byte
-// aligned, bytes a multiple of 16 (0 < bytes < 2^20).
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-// Bounded wait on an mbarrier phase (no unbounded spin anywhere): returns
-// false after `limit` polls of at most ~100 us each.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
-  const uint32_t addr = (uint32_t)__cvta_generic_to_shared(bar);
-  for (uint32_t i = 0; i < limit; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity), "r"(100000u)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
 }  // namespace gbar

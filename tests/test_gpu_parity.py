@@ -244,3 +244,80 @@ def test_batched_repeated_launches_reuse_workspace(gb, orc):
                 assert np.array_equal(idx.cpu().numpy(), oidx)
         assert work[:16].cpu().numpy().tolist() == [0] * 16
     assert int(st.item()) == 0
+
+
+# ------------------------------------------- ar_bound_batched / _bounded
+@pytest.mark.parametrize("plan", [False, True])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_bound_batched(gb, orc, dtype, plan):
+    """The reduction step alone: exact maxima, totals within the FP64 bound,
+    ALL_ZERO for an all-zero realization and for M_b = 0."""
+    vecs = [W.wide_range(m, seed=m).astype(dtype) for m in (1, 3, 1000, 1025, 4099, 20_000)]
+    vecs += [np.zeros(17, dtype=dtype), np.zeros(0, dtype=dtype), W.skewed(3000).astype(dtype)]
+    bt = W.batch_from_vectors(vecs, [1] * len(vecs))
+    pl = gb.Plan(bt.offsets, bt.out_offsets) if plan else None
+    bs, st = gb.bound_batched(_t(bt.alpha), _t(bt.offsets), plan=pl)
+    got = bs.cpu().numpy()
+    for b, a in enumerate(vecs):
+        mx, sm, _ = orc.bound(a)
+        assert got[b, 0] == mx, b
+        assert abs(got[b, 1] - sm) <= _sum_tol(a, sm), b
+    assert int(st.item()) == gb.AR_STATUS_ALL_ZERO
+
+
+@pytest.mark.parametrize("plan", [False, True])
+@pytest.mark.parametrize("w", [1.0, 1.5, 2.0, 4.0])
+def test_select_batched_bounded_threshold_sweep(gb, orc, w, plan):
+    """T_w = w max per realization (the paper's threshold experiment): indices
+    and trial counts bit-exact against the oracle at every w."""
+    bt = W.batched_uneven(B=300, seed=303, K=128)
+    bs_o, _, _, _ = orc.select_batched(bt)
+    T = w * bs_o[:, 0]
+    pl = gb.Plan(bt.offsets, bt.out_offsets) if plan else None
+    idx, stats, st = gb.select_batched_bounded(_t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets),
+                                               _t(T), seed=4, sel_offset=9, plan=pl)
+    oidx, ostats, ost = orc.select_batched_bounded(bt, T, seed=4, sel_offset=9, nthreads=8)
+    np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
+    np.testing.assert_array_equal(stats.cpu().numpy().astype(np.uint64), ostats)
+    assert int(st.item()) == ost
+
+
+def test_select_batched_bounded_stride_and_bad_bounds(gb, orc):
+    """Stride 2 over a bound_sum array; NaN, negative and infinite bounds give
+    BAD_BOUND and the sentinel; a zero bound gives ALL_ZERO."""
+    bt = W.batched_uneven(B=40, seed=304, m_lo=8, m_hi=3000, K=50)
+    bs, _ = gb.bound_batched(_t(bt.alpha), _t(bt.offsets))
+    idx, stats, st = gb.select_batched_bounded(_t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets),
+                                               bs, bound_stride=2)
+    _, oidx, ostats, ost = orc.select_batched(bt)
+    np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
+    assert int(st.item()) == ost
+    T = bs[:, 0].cpu().numpy().copy()
+    T[3], T[7], T[11], T[20] = np.nan, -2.0, np.inf, 0.0
+    for cmp in (0, 1):
+        idx, _, st = gb.select_batched_bounded(_t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets),
+                                               _t(T), cmp=cmp)
+        oidx, _, ost = orc.select_batched_bounded(bt, T, cmp=cmp)
+        np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
+        assert int(st.item()) == ost == gb.AR_STATUS_BAD_BOUND | gb.AR_STATUS_ALL_ZERO
+
+
+@pytest.mark.parametrize("plan", [False, True])
+def test_batched_invalid_realization(gb, orc, plan):
+    """A realization holding NaN / -1 / inf: BAD_ALPHA, (NaN, NaN) bound, the
+    sentinel for its indices; the other realizations are unaffected."""
+    bt = W.batched_uneven(B=64, seed=305, m_lo=16, m_hi=5000, K=40)
+    a = bt.alpha.copy()
+    a[bt.offsets[5] + 2] = np.nan
+    a[bt.offsets[17]] = -1.0
+    a[bt.offsets[40] + 1] = np.inf
+    bt2 = W.Batch(a, bt.offsets, bt.out_offsets)
+    pl = gb.Plan(bt.offsets, bt.out_offsets) if plan else None
+    bs, idx, stats, st = gb.select_batched(_t(a), _t(bt.offsets), _t(bt.out_offsets), plan=pl)
+    obs, oidx, ostats, ost = orc.select_batched(bt2, nthreads=8)
+    np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
+    np.testing.assert_array_equal(stats.cpu().numpy().astype(np.uint64), ostats)
+    g = bs.cpu().numpy()
+    np.testing.assert_array_equal(np.isnan(g), np.isnan(obs))
+    np.testing.assert_array_equal(g[~np.isnan(g[:, 0]), 0], obs[~np.isnan(obs[:, 0]), 0])
+    assert int(st.item()) == ost == gb.AR_STATUS_BAD_ALPHA

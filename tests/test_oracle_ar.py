@@ -223,3 +223,57 @@ def test_batched_oracle_matches_single(orc):
         ib, _, _ = orc.select_ar(a, 40, seed=2, sel_offset=7, realization=10 + b, cmp=0)
         np.testing.assert_array_equal(idx[bt.out_offsets[b]:bt.out_offsets[b + 1]], ib)
     assert int(stats[1]) == 6 * 40
+
+
+def test_batched_invalid_realization(orc):
+    """A realization with an invalid propensity has no usable bound: (NaN, NaN),
+    every index the sentinel M_b, BAD_ALPHA; the others are unaffected."""
+    bt = W.batched_uneven(B=5, seed=4, m_lo=8, m_hi=200, K=30)
+    bad = bt.alpha.copy()
+    bad[bt.offsets[2] + 3] = np.nan
+    bt2 = W.Batch(bad, bt.offsets, bt.out_offsets)
+    bs, idx, _, st = orc.select_batched(bt)
+    bs2, idx2, _, st2 = orc.select_batched(bt2)
+    assert st2 & orc.ST_BAD_ALPHA and not st & orc.ST_BAD_ALPHA
+    assert np.isnan(bs2[2]).all()
+    M2 = bt.offsets[3] - bt.offsets[2]
+    np.testing.assert_array_equal(idx2[bt.out_offsets[2]:bt.out_offsets[3]], M2)
+    keep = np.ones(idx.size, bool)
+    keep[bt.out_offsets[2]:bt.out_offsets[3]] = False
+    np.testing.assert_array_equal(idx2[keep], idx[keep])
+
+
+@pytest.mark.parametrize("w", [1.5, 2.0, 4.0])
+def test_threshold_sweep_trials_and_law(orc, w):
+    """T_w = w max (the paper's threshold experiment): the expected number of
+    trials per selection is M T_w / sum(alpha) (geometric with success
+    probability sum(alpha) / (M T_w)), and the law stays exact."""
+    a = W.plain_uniform(200, seed=21)
+    bt = W.batch_from_vectors([a], [60_000])
+    T = w * float(a.max())
+    idx, stats, st = orc.select_batched_bounded(bt, [T], nthreads=8)
+    assert st == 0
+    p = math.fsum(a.tolist()) / (a.size * T)
+    mean_t = float(stats[0]) / 60_000
+    sd = math.sqrt((1 - p) / p ** 2 / 60_000)
+    assert abs(mean_t - 1 / p) < 4 * sd, (mean_t, 1 / p, sd)
+    assert law.chi_square(np.bincount(idx, minlength=a.size), law.exact_law(a)) > 1e-3
+
+
+def test_bounded_batched_with_own_maxima_equals_batched(orc):
+    """Bounds equal to each realization's maximum reproduce ar_select_batched;
+    stride 2 reads a bound_sum array; bad bounds give BAD_BOUND and M_b."""
+    bt = W.batched_uneven(B=7, seed=8, m_lo=4, m_hi=500, K=25)
+    bs, idx, stats, st = orc.select_batched(bt, seed=3, sel_offset=5, realization_base=2)
+    idx2, stats2, st2 = orc.select_batched_bounded(bt, bs.ravel(), stride=2, seed=3, sel_offset=5,
+                                                   realization_base=2)
+    np.testing.assert_array_equal(idx2, idx)
+    np.testing.assert_array_equal(stats2, stats)
+    assert st2 == st
+    T = bs[:, 0].copy()
+    T[1], T[4] = np.nan, -1.0
+    idx3, _, st3 = orc.select_batched_bounded(bt, T, seed=3, sel_offset=5, realization_base=2)
+    assert st3 & orc.ST_BAD_BOUND
+    for b in (1, 4):
+        sl = slice(bt.out_offsets[b], bt.out_offsets[b + 1])
+        assert (idx3[sl] == bt.offsets[b + 1] - bt.offsets[b]).all()
