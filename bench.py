@@ -1,8 +1,9 @@
 #!/usr/bin/env python3
 """Benchmark of the batched AR selection hot path on GB300.
 
-One step = one ``ar_select_batched`` launch (bound/sum reduction, Philox
-trials, gathers, ballot compaction and output for every realization) on the
+One step = one ``ar_select_batched`` call (bound/sum reduction, Philox
+trials, gathers, ballot compaction and output for every realization; three
+kernels) on the
 batched-uneven workload: B = 4096 realizations, M_b log-uniform in
 [64, 16384], alpha FP32 Exponential(1), K_b = 256 selections each, FP32
 comparison.  The launch is replayed from a captured CUDA graph.  Inputs are
@@ -49,7 +50,7 @@ IMAD_PER_SM_CLK = 64             # 32-bit integer multiply-add issue rate per SM
 def workload_config():
     return {"workload": f"batched-uneven: B={B_REAL} realizations, M_b log-uniform "
                         f"[{M_LO},{M_HI}], alpha FP32 Exponential(1), K_b={K_B}, FP32 comparison, "
-                        "one persistent launch per step from a CUDA graph",
+                        "one ar_select_batched call (3 kernels) per step from a CUDA graph",
             "B": B_REAL, "K_b": K_B, "M_range": [M_LO, M_HI], "cmp": "f32", "seed": SEED,
             "l2": f"inputs rotated over {N_SLOTS} independently drawn batches "
                   f"(~{N_SLOTS * 52} MB > 129 MB L2)"}
@@ -169,6 +170,11 @@ def gpu_id_for(torch, dev) -> str:
 def algorithmic_bytes(bt) -> int:
     """alpha read once + both offset arrays read + indices and (max, sum) written."""
     return 4 * int(bt.offsets[-1]) + 16 * (bt.B + 1) + 4 * int(bt.out_offsets[-1]) + 16 * bt.B
+
+
+def reduction_bytes(bt) -> int:
+    """The reduction step: alpha and the offsets read once, (max, sum) written."""
+    return 4 * int(bt.offsets[-1]) + 8 * (bt.B + 1) + 16 * bt.B
 
 
 # --------------------------------------------------------------------------
@@ -376,27 +382,76 @@ def main():
         accepted_all = accepted
     value = accepted_all / (elapsed_ms * 1e-3)
 
-    # ---- roofline of the batched kernel ----------------------------------
+    # ---- per-kernel durations: the two steps of the call, each replayed
+    # alone from its own graphs (CUDA events on the launching stream) -----
+    for s in slots:
+        s["st2"] = torch.zeros(1, dtype=torch.int32, device=dev)
+        s["stats2"] = torch.zeros(3, dtype=torch.int64, device=dev)
+
+    def bound_only(s):
+        gb.ar_bound_batched(s["alpha"], s["off"], s["plan"], s["bs"], s["st2"], s["work"], stream)
+
+    def select_only(s):  # bounds from the last full step on this batch
+        gb.ar_select_batched_bounded(s["alpha"], s["off"], s["oo"], s["bs"], 2, SEED, 0, b_base,
+                                     gb.AR_CMP_F32, 1 << 20, s["plan"], s["idx"], s["stats2"],
+                                     s["st2"], s["work"], stream)
+
+    def time_alone(fn, reps):
+        gs = []
+        for s in slots:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                fn(s)
+            gs.append(g)
+        for i in range(3 * N_SLOTS):
+            gs[i % N_SLOTS].replay()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(reps)]
+        with torch.cuda.stream(stream):
+            for i in range(reps):
+                evs[i][0].record(stream)
+                gs[i % N_SLOTS].replay()
+                evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return np.array([x.elapsed_time(y) for x, y in evs])
+
+    reps = min(K, 3000)
+    red_ms = time_alone(bound_only, reps)
+    sel_ms = time_alone(select_only, reps)
+
+    # ---- rooflines ---------------------------------------------------------
     peak, peak_kind, peaks = measured_peaks()
-    alg_bytes = float(np.mean([algorithmic_bytes(s["bt"]) for s in slots]))
-    kmean_s = float(kern_ms.mean()) * 1e-3
-    achieved = alg_bytes / kmean_s / 1e9
-    traffic = profiled_traffic("batched_select_cfg_batched_uneven.md")
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
-                "kernel": "ar_select_batched step (k_bound_reg + k_batched_combine + "
-                          "k_batched_select<float, AR_CMP_F32>)",
-                "algorithmic_bytes_per_launch": alg_bytes,
-                "kernel_ms_mean": kmean_s * 1e3, "kernel_ms_median": float(np.median(kern_ms))}
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clk = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = IMAD_PER_SM_CLK * sm_count * clk * 1e6 / PHILOX_IMAD_PER_BLOCK
     blocks_per_launch = trials / K / 2.0
-    alu = {"bound": "alu", "achieved": blocks_per_launch / kmean_s, "peak": alu_peak,
-           "unit": "Philox4x32-10 blocks/s", "frac": blocks_per_launch / kmean_s / alu_peak,
-           "peak_from": f"{IMAD_PER_SM_CLK} IMAD/clk/SM x {sm_count} SMs x {clk:.0f} MHz / "
-                        f"{PHILOX_IMAD_PER_BLOCK} IMAD per block",
-           "trials_per_launch": trials / K}
+    sel_s = float(sel_ms.mean()) * 1e-3
+    red_s = float(red_ms.mean()) * 1e-3
+    # the dominant kernel: the selections, bound by 32-bit integer multiply
+    # issue (Philox); work = the Philox blocks the accepted trials need
+    roofline = {"bound": "alu", "achieved": blocks_per_launch / sel_s, "peak": alu_peak,
+                "unit": "Philox4x32-10 blocks/s", "frac": blocks_per_launch / sel_s / alu_peak,
+                "traffic": profiled_traffic("k_batched_select_batched_uneven.md"),
+                "kernel": "k_batched_select<float, AR_CMP_F32>",
+                "peak_from": f"{IMAD_PER_SM_CLK} IMAD/clk/SM x {sm_count} SMs x {clk:.0f} MHz / "
+                             f"{PHILOX_IMAD_PER_BLOCK} IMAD per block",
+                "work_per_launch": blocks_per_launch, "trials_per_launch": trials / K,
+                "kernel_ms_mean": sel_s * 1e3, "kernel_ms_median": float(np.median(sel_ms))}
+    red_bytes = float(np.mean([reduction_bytes(s["bt"]) for s in slots]))
+    roofline_reduction = {
+        "bound": "hbm", "achieved": red_bytes / red_s / 1e9, "peak": peak, "unit": "GB/s",
+        "frac": red_bytes / red_s / 1e9 / peak, "peak_kind": peak_kind,
+        "traffic": profiled_traffic("k_bound_reg_batched_uneven.md"),
+        "kernel": "k_bound_reg + k_batched_combine (ar_bound_batched)",
+        "algorithmic_bytes_per_launch": red_bytes, "kernel_ms_mean": red_s * 1e3,
+        "kernel_ms_median": float(np.median(red_ms))}
+    alg_bytes = float(np.mean([algorithmic_bytes(s["bt"]) for s in slots]))
+    step_s = float(kern_ms.mean()) * 1e-3
+    step_hbm = {"bound": "hbm", "achieved": alg_bytes / step_s / 1e9, "peak": peak,
+                "unit": "GB/s", "frac": alg_bytes / step_s / 1e9 / peak, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_step": alg_bytes, "step_ms_mean": step_s * 1e3,
+                "share_reduction": red_s / (red_s + sel_s), "share_selection": sel_s / (red_s + sel_s)}
 
     # ---- end to end through the C ABI with host buffers ------------------
     ke = min(K, 100)
@@ -546,7 +601,8 @@ def main():
                    "indices_match_device_run": e2e_ok},
            "gpu_launches": K * LAUNCHES_PER_CALL,
            "roofline": roofline,
-           "alu_roofline": alu,
+           "roofline_reduction": roofline_reduction,
+           "step_hbm": step_hbm,
            "cpu_baseline": cpu,
            "fp64_plain": fp64_plain,
            "ssa": ssa,
