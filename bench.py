@@ -167,6 +167,35 @@ def gpu_id_for(torch, dev) -> str:
         return vis.split(",")[dev.index or 0] if vis else str(dev.index or 0)
 
 
+# --------------------------------------------------------------------------
+# Multi-rank helpers (one process per GPU; realizations shard by rank, no
+# data-path collective -- only the timing and count reductions below)
+# --------------------------------------------------------------------------
+def rank_realization_base(rank: int, B: int) -> int:
+    """Philox realization ids of rank r: [r B, (r + 1) B), disjoint across ranks,
+    so every rank's streams equal those of one run over all realizations."""
+    return rank * B
+
+
+def reduce_max(value: float, dist, device) -> float:
+    """Max over ranks (the slowest rank's time defines the job's time)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, dist, device) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t)
+    return float(t.item())
+
+
 def algorithmic_bytes(bt) -> int:
     """alpha read once + both offset arrays read + indices and (max, sum) written."""
     return 4 * int(bt.offsets[-1]) + 16 * (bt.B + 1) + 4 * int(bt.out_offsets[-1]) + 16 * bt.B
@@ -291,7 +320,7 @@ def main():
              # schedule built once per batch shape (host LPT over the CTAs)
              "plan": gb.Plan(bt.offsets, bt.out_offsets)}
         slots.append(s)
-    b_base = rank * B_REAL
+    b_base = rank_realization_base(rank, B_REAL)
     stream = torch.cuda.Stream(dev)
 
     def launch(s, cmp=gb.AR_CMP_F32, idx=None):
@@ -371,15 +400,8 @@ def main():
     status = 0
     for s in slots:
         status |= int(s["st"].item())
-    if dist:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-        a = torch.tensor([accepted], dtype=torch.float64, device=dev)
-        dist.all_reduce(a)
-        accepted_all = int(a.item())
-    else:
-        accepted_all = accepted
+    elapsed_ms = reduce_max(elapsed_ms, dist, dev)
+    accepted_all = int(reduce_sum(accepted, dist, dev))
     value = accepted_all / (elapsed_ms * 1e-3)
 
     # ---- per-kernel durations: the two steps of the call, each replayed
@@ -488,10 +510,7 @@ def main():
         e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = reduce_max(e2e_ms, dist, dev)
     e2e_value = world * ke * B_REAL * K_B / (e2e_ms * 1e-3)
     e2e_ok = bool(np.array_equal(h_idx.numpy(), g_idx))
 
