@@ -270,6 +270,46 @@ int ar_select_batched(const void *d_alpha_cat, int dtype, const int64_t *d_offse
                       void *d_work, size_t work_bytes, void *stream);
 
 /* ---------------------------------------------------------------------
+ * ar_select_paper -- the paper's own GPU selection rule, for comparison
+ * (Sections "Election step" and "Selection step", the Results'
+ * pseudo-code; its quality experiment, Table 1).  FP32, as the paper's
+ * arrays are float.  For selection s (id sel_offset + i) every reaction j
+ * draws u_j = floor(w / 2^8) 2^-24 (counter (j/2, s, realization, 3), word
+ * 2(j mod 2) + 1) and is eligible when fl(u_j T) < D_j and D_j != 0, with
+ * rate R_j = fl(fl(u_j T) / D_j); the selection is argmin R (lowest j on
+ * ties), or the sentinel M when min R >= 1 (a rejection).  The rule's law
+ * differs from D_j / sum D (the bias that Table 1 measures).
+ *   d_D          [M] FP32, 0 <= M < 2^31.
+ *   d_bound      device double; T = fl32(*d_bound) (the paper's T_w).
+ *   K            selections, sel_offset + K <= 2^32.
+ *   d_idx        [K] int32 out.
+ *   d_rejections nullable device uint64 accumulator of rejections.
+ * ------------------------------------------------------------------- */
+int ar_select_paper(const float *d_D, int64_t M, const double *d_bound, int64_t K,
+                    uint64_t seed, uint64_t sel_offset, uint32_t realization, int32_t *d_idx,
+                    unsigned long long *d_rejections, void *stream);
+
+/* ---------------------------------------------------------------------
+ * ar_select_it -- the direct method's inverse transform, the comparator
+ * the paper argues against (Section "The Stochastic Simulation
+ * Algorithm": j is the smallest index with alpha_0 + ... + alpha_j >
+ * u alpha_0).  The running sums are the sequential FP64 sums in index
+ * order (computed once per call by one thread, into the workspace);
+ * u = (w0 2^21 + floor(w1 / 2^11)) 2^-53 from counter (0, s, realization,
+ * 2); if rounding leaves no running sum above the target, the last
+ * non-zero index is taken; alpha_0 <= 0 (or NaN) gives the sentinel M.
+ *   d_alpha      [M] FP32/FP64 (dtype).
+ *   d_idx        [K] int32 out.
+ *   d_status     OR-ed with BAD_ALPHA and ALL_ZERO (as ar_bound).
+ *   d_work       ar_select_it_workspace_size(M) bytes, 16-byte aligned,
+ *                rewritten by every call.  Calls sharing it must not overlap.
+ * ------------------------------------------------------------------- */
+size_t ar_select_it_workspace_size(int64_t M);
+int ar_select_it(const void *d_alpha, int dtype, int64_t M, int64_t K, uint64_t seed,
+                 uint64_t sel_offset, uint32_t realization, int32_t *d_idx, uint32_t *d_status,
+                 void *d_work, size_t work_bytes, void *stream);
+
+/* ---------------------------------------------------------------------
  * SSA step (Section "The Stochastic Simulation Algorithm": select j, draw
  * tau = ln(1/u)/a_0, X += v_j, t += tau; the selection is the AR trial
  * above with T = max_j a_j and selection id = the realization's step

@@ -66,6 +66,9 @@ SIGNATURES = {
     "ar_select_batched": (_int, [_vp, _int, _vp, _vp, _i64, _u64, _u64, _u32, _int, _u64, _vp,
                                  _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "ar_bound_batched": (_int, [_vp, _int, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "ar_select_paper": (_int, [_vp, _i64, _vp, _i64, _u64, _u64, _u32, _vp, _vp, _vp]),
+    "ar_select_it_workspace_size": (_sz, [_i64]),
+    "ar_select_it": (_int, [_vp, _int, _i64, _i64, _u64, _u64, _u32, _vp, _vp, _vp, _sz, _vp]),
     "ar_select_batched_bounded": (_int, [_vp, _int, _vp, _vp, _i64, _vp, _i64, _u64, _u64, _u32,
                                          _int, _u64, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
 }
@@ -287,6 +290,45 @@ def select_batched(alpha_cat, offsets, out_offsets, seed=1, sel_offset=0, realiz
     ar_select_batched(alpha_cat, offsets, out_offsets, seed, sel_offset, realization_base, cmp,
                       trial_cap, plan, bs, idx, stats, st, work, stream)
     return bs, idx, stats, st
+
+
+def ar_select_paper(D, bound, K, seed, sel_offset, realization, idx, rejections, stream=None):
+    _check(lib().ar_select_paper(
+        _dev(D, torch.float32, "D"), D.numel(), _dev(bound, torch.float64, "bound"), K, seed,
+        sel_offset, realization, _dev(idx, torch.int32, "idx"),
+        _dev(rejections, torch.int64, "rejections"), _stream(stream)), "ar_select_paper")
+
+
+def ar_select_it_workspace_size(M: int) -> int:
+    return int(lib().ar_select_it_workspace_size(M))
+
+
+def ar_select_it(alpha, K, seed, sel_offset, realization, idx, status, work, stream=None):
+    nbytes = 0 if work is None else work.numel() * work.element_size()
+    _check(lib().ar_select_it(
+        _dev(alpha, name="alpha"), _dtype_code(alpha), alpha.numel(), K, seed, sel_offset,
+        realization, _dev(idx, torch.int32, "idx"), _dev(status, torch.int32, "status"),
+        _dev(work, name="work"), nbytes, _stream(stream)), "ar_select_it")
+
+
+def select_paper(D, K, T, seed=1, sel_offset=0, realization=0, stream=None):
+    """The paper's election rule -> (idx int32[K], rejections int64[1])."""
+    dev = D.device
+    idx = torch.empty(K, dtype=torch.int32, device=dev)
+    rej = torch.zeros(1, dtype=torch.int64, device=dev)
+    bound = torch.tensor([float(T)], dtype=torch.float64, device=dev)
+    ar_select_paper(D, bound, K, seed, sel_offset, realization, idx, rej, stream)
+    return idx, rej
+
+
+def select_it(alpha, K, seed=1, sel_offset=0, realization=0, stream=None):
+    """Inverse transform -> (idx int32[K], status int32[1])."""
+    dev = alpha.device
+    idx = torch.empty(K, dtype=torch.int32, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    work = torch.empty(ar_select_it_workspace_size(alpha.numel()), dtype=torch.uint8, device=dev)
+    ar_select_it(alpha, K, seed, sel_offset, realization, idx, st, work, stream)
+    return idx, st
 
 
 def bound_batched(alpha_cat, offsets, plan=None, stream=None):
