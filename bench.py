@@ -50,7 +50,8 @@ IMAD_PER_SM_CLK = 64             # 32-bit integer multiply-add issue rate per SM
 def workload_config():
     return {"workload": f"batched-uneven: B={B_REAL} realizations, M_b log-uniform "
                         f"[{M_LO},{M_HI}], alpha FP32 Exponential(1), K_b={K_B}, FP32 comparison, "
-                        "one ar_select_batched call (3 kernels) per step from a CUDA graph",
+                        "one ar_select_batched call (3 kernels) per step from a CUDA graph, "
+                        "selection tiles picked per batch by ar_plan_autotune",
             "B": B_REAL, "K_b": K_B, "M_range": [M_LO, M_HI], "cmp": "f32", "seed": SEED,
             "l2": f"inputs rotated over {N_SLOTS} independently drawn batches "
                   f"(~{N_SLOTS * 52} MB > 129 MB L2)"}
@@ -329,6 +330,12 @@ def main():
                              s["bs"], s["idx"] if idx is None else idx, s["stats"], s["st"],
                              s["work"], stream)
 
+    # tile shape of the selection kernel per batch, picked by the autotuner
+    tuned = []
+    for s in slots:
+        tuned.append(gb.ar_plan_autotune(s["plan"], s["alpha"], s["off"], s["oo"], SEED,
+                                         gb.AR_CMP_F32, s["bs"], s["idx"], s["stats"], s["st"],
+                                         reps=10, stream=stream))
     with torch.cuda.stream(stream):
         launch(slots[0])
     stream.synchronize()
@@ -640,7 +647,9 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
            "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": workload_config(),
+           "config": dict(workload_config(),
+                          autotuned_tiles=[{"warps_per_cta": t[0], "global_share_pm": t[1],
+                                            "ns_per_call": t[2]} for t in tuned]),
            "clocks": clocks,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": e2e_ms / ke,

@@ -245,8 +245,10 @@ int ar_select_batched_bounded(const void *d_alpha_cat, int dtype, const int64_t 
  *     realizations (estimated cost K_b (0.6 + ln M_b) + 0.05 M_b) are
  *     assigned to the persistent CTAs of the selection kernel by
  *     longest-processing-time-first list scheduling (each CTA's home list);
- *     the cheapest ones, 30% of the estimated cost, form a global queue
- *     that balances the CTAs' finishing times (32 bytes per range);
+ *     the cheapest ones, 30% of the estimated cost by default, form a
+ *     global queue that balances the CTAs' finishing times (32 bytes per
+ *     range).  Default tile: 16 warps per CTA, 2 CTAs per SM;
+ *     ar_plan_autotune picks tile and share on the caller's data;
  *   - device scratch for the chunk partials (32 bytes per chunk).
  * Results are identical with or without a plan.  Calls sharing a plan must
  * not overlap on the GPU (they share its scratch).
@@ -262,6 +264,27 @@ int ar_select_batched_bounded(const void *d_alpha_cat, int dtype, const int64_t 
 int ar_plan_create(const int64_t *h_offsets, const int64_t *h_out_offsets, int64_t B,
                    ar_plan **out);
 void ar_plan_destroy(ar_plan *plan);
+
+/* ---------------------------------------------------------------------
+ * ar_plan_autotune -- picks the selection kernel's tile shape for a plan
+ * by timing it on the caller's data (the batched workload's block/warp
+ * tiles): warps per CTA in {16, 32, 8} (1024 threads per SM) times the
+ * share of the estimated cost left to the global queue in {0, 0.3, 0.6}.
+ * Each candidate rebuilds the plan's selection schedule (host), runs two
+ * warm-up calls and `reps` timed calls of ar_select_batched (seed,
+ * sel_offset 0, realization_base 0, trial_cap 2^20, the given cmp) on
+ * `stream`, timed with CUDA events; the fastest is kept.  Results of
+ * ar_select_batched do not depend on the choice.  Synchronous (blocks the
+ * host; not capturable).  d_bound_sum, d_idx, d_stats, d_status receive the
+ * tuning calls' outputs (stats and status accumulate).
+ *   h_choice   nullable host int32[3]: warps per CTA, global share per
+ *              mille, mean nanoseconds per call of the choice.
+ * Errors: as ar_select_batched; AR_ERR_ARG for reps outside 1..10000.
+ * ------------------------------------------------------------------- */
+int ar_plan_autotune(ar_plan *plan, const void *d_alpha_cat, int dtype,
+                     const int64_t *d_offsets, const int64_t *d_out_offsets, uint64_t seed,
+                     int cmp, double *d_bound_sum, int32_t *d_idx, ar_stats *d_stats,
+                     uint32_t *d_status, int reps, int32_t *h_choice, void *stream);
 int ar_select_batched(const void *d_alpha_cat, int dtype, const int64_t *d_offsets,
                       const int64_t *d_out_offsets, int64_t B, uint64_t seed,
                       uint64_t sel_offset, uint32_t realization_base, int cmp,

@@ -67,6 +67,8 @@ SIGNATURES = {
                                  _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "ar_bound_batched": (_int, [_vp, _int, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
     "ar_select_paper": (_int, [_vp, _i64, _vp, _i64, _u64, _u64, _u32, _vp, _vp, _vp]),
+    "ar_plan_autotune": (_int, [_vp, _vp, _int, _vp, _vp, _u64, _int, _vp, _vp, _vp, _vp, _int,
+                                _vp, _vp]),
     "ar_select_it_workspace_size": (_sz, [_i64]),
     "ar_select_it": (_int, [_vp, _int, _i64, _i64, _u64, _u64, _u32, _vp, _vp, _vp, _sz, _vp]),
     "ar_select_batched_bounded": (_int, [_vp, _int, _vp, _vp, _i64, _vp, _i64, _u64, _u64, _u32,
@@ -290,6 +292,20 @@ def select_batched(alpha_cat, offsets, out_offsets, seed=1, sel_offset=0, realiz
     ar_select_batched(alpha_cat, offsets, out_offsets, seed, sel_offset, realization_base, cmp,
                       trial_cap, plan, bs, idx, stats, st, work, stream)
     return bs, idx, stats, st
+
+
+def ar_plan_autotune(plan, alpha_cat, offsets, out_offsets, seed, cmp, bound_sum, idx, stats,
+                     status, reps=20, stream=None):
+    """Times the plan's selection tile candidates on this data and keeps the
+    fastest -> (warps per CTA, global share per mille, ns per call)."""
+    choice = (ctypes.c_int32 * 3)()
+    _check(lib().ar_plan_autotune(
+        _plan_ptr(plan), _dev(alpha_cat, name="alpha_cat"), _dtype_code(alpha_cat),
+        _dev(offsets, torch.int64, "offsets"), _dev(out_offsets, torch.int64, "out_offsets"),
+        seed, cmp, _dev(bound_sum, torch.float64, "bound_sum"), _dev(idx, torch.int32, "idx"),
+        _dev(stats, torch.int64, "stats"), _dev(status, torch.int32, "status"), reps, choice,
+        _stream(stream)), "ar_plan_autotune")
+    return tuple(int(x) for x in choice)
 
 
 def ar_select_paper(D, bound, K, seed, sel_offset, realization, idx, rejections, stream=None):

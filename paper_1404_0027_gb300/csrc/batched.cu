@@ -48,9 +48,10 @@
 namespace gbar {
 namespace {
 
-constexpr int kWarps = 16;  // selection kernel
-constexpr int kNT = kWarps * 32;
-constexpr int kCtasPerSm = 2;
+// selection kernel tile shapes (warps per CTA; 1024 threads per SM): the
+// plan's default and the autotuner's candidates
+constexpr int kSelShapes[3] = {16, 32, 8};
+constexpr int kSelThreadsPerSm = 1024;
 constexpr int kBWarps = 8;  // reduction kernels
 constexpr int kBNT = kBWarps * 32;
 constexpr int kBCtasPerSm = 2;
@@ -58,7 +59,6 @@ constexpr uint32_t kChunk = 1024;  // reduction chunk (elements)
 constexpr int kVPL = kChunk / 32;  // elements per lane (register path)
 constexpr uint32_t kSItem = 32;     // selections per home work item
 constexpr uint32_t kGItem = 32;     // selections per global-queue work item
-constexpr double kGlobalShare = 0.3;  // estimated cost left to the global queue
 constexpr int kU = 2;               // Philox blocks per lane per round
 
 // ---- plan-built work items -------------------------------------------------
@@ -763,9 +763,10 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
   }
 }
 
-template <typename TS, int CMP>
-__global__ void __launch_bounds__(kNT, kCtasPerSm) k_batched_select(const Params p) {
-  __shared__ uint32_t s_scr[kWarps * 64];
+template <typename TS, int CMP, int NW>
+__global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
+    k_batched_select(const Params p) {
+  __shared__ uint32_t s_scr[NW * 64];
   __shared__ uint32_t s_queue;
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt = (1u << lane) - 1u;
@@ -950,12 +951,16 @@ int launch_bound(const Params& p, bool stream_path, cudaStream_t s) {
   return check_launch();
 }
 
-// The selection kernel (bounds from p.bound_in).
+// The selection kernel (bounds from p.bound_in) with tile shape `shape`.
 template <typename TS, int CMP>
-int launch_select(const Params& p, uint32_t sel_grid, cudaStream_t s) {
+int launch_select(const Params& p, uint32_t sel_grid, int shape, cudaStream_t s) {
   const DeviceInfo& d = device_info();
   const uint32_t sms = (uint32_t)(d.sm_count > 0 ? d.sm_count : 1);
-  k_batched_select<TS, CMP><<<sel_grid ? sel_grid : sms * kCtasPerSm, kNT, 0, s>>>(p);
+  const int nw = kSelShapes[shape];
+  const uint32_t grid = sel_grid ? sel_grid : sms * (uint32_t)(kSelThreadsPerSm / (nw * 32));
+  if (nw == 32) k_batched_select<TS, CMP, 32><<<grid, 32 * 32, 0, s>>>(p);
+  else if (nw == 8) k_batched_select<TS, CMP, 8><<<grid, 8 * 32, 0, s>>>(p);
+  else k_batched_select<TS, CMP, 16><<<grid, 16 * 32, 0, s>>>(p);
   return check_launch();
 }
 
@@ -971,29 +976,150 @@ struct ar_plan {
   int device;
   int64_t B;
   uint32_t nr, ns, grid, gq0;
+  int shape;            // selection tile shape (index into kSelShapes)
+  int gshare_pm;        // estimated cost left to the global queue, per mille
   RItem* d_ritems;
   RInfo* d_rinfo;
   SItem* d_sitems;
+  size_t sitems_cap;    // SItem capacity of d_sitems
   uint32_t* d_scta;
+  size_t scta_cap;
   unsigned char* d_scratch;  // Scratch | parts[NR]
+  std::vector<int64_t> off, oo;  // host copies of the offsets (schedule rebuilds)
+  std::vector<double> cost;
 };
+
+namespace {
+
+// The selection schedule for `grid` CTAs: realizations by decreasing
+// estimated cost; the costliest go to the CTAs' home lists (longest
+// processing time first onto the least loaded CTA) until the cost left is
+// gshare of the total; the rest form the global queue in that order.
+void build_selection(const ar_plan& pl, uint32_t grid, double gshare, std::vector<SItem>& sitems,
+                     std::vector<uint32_t>& scta, uint32_t& gq0) {
+  const int64_t B = pl.B;
+  double total_cost = 0.0;
+  for (double c : pl.cost) total_cost += c;
+  std::vector<int64_t> order(B);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int64_t x, int64_t y) { return pl.cost[x] > pl.cost[y]; });
+  using Load = std::pair<double, uint32_t>;
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (uint32_t c = 0; c < grid; ++c) heap.push({0.0, c});
+  std::vector<std::vector<int64_t>> lists(grid);
+  double left = total_cost;
+  size_t n_home = 0;
+  for (; n_home < order.size() && left > gshare * total_cost; ++n_home) {
+    const int64_t b = order[n_home];
+    Load l = heap.top();
+    heap.pop();
+    lists[l.second].push_back(b);
+    l.first += pl.cost[b];
+    heap.push(l);
+    left -= pl.cost[b];
+  }
+  sitems.clear();
+  auto add_items = [&](int64_t b, uint32_t per) {
+    const uint32_t K = (uint32_t)(pl.oo[b + 1] - pl.oo[b]);
+    uint32_t s0 = 0;
+    do {  // one item even when K = 0
+      SItem s{};
+      s.a0 = pl.off[b];
+      s.o0 = pl.oo[b];
+      s.M = (uint32_t)(pl.off[b + 1] - pl.off[b]);
+      s.b = (uint32_t)b;
+      s.s0 = s0;
+      s.s1 = (uint32_t)std::min<uint64_t>(K, (uint64_t)s0 + per);
+      sitems.push_back(s);
+      s0 = s.s1;
+    } while (s0 < K);
+  };
+  scta.assign(grid + 1, 0);
+  for (uint32_t c = 0; c < grid; ++c) {
+    for (int64_t b : lists[c]) add_items(b, kSItem);
+    scta[c + 1] = (uint32_t)sitems.size();
+  }
+  gq0 = (uint32_t)sitems.size();
+  for (size_t k = n_home; k < order.size(); ++k) add_items(order[k], kGItem);
+}
+
+// Rebuilds and uploads the plan's selection schedule for a tile shape and
+// global-queue share (synchronous).
+int set_schedule(ar_plan& pl, int shape, int gshare_pm) {
+  const DeviceInfo& dev = device_info();
+  const uint32_t grid = (uint32_t)std::max(1, dev.sm_count) *
+                        (uint32_t)(kSelThreadsPerSm / (kSelShapes[shape] * 32));
+  std::vector<SItem> sitems;
+  std::vector<uint32_t> scta;
+  uint32_t gq0 = 0;
+  build_selection(pl, grid, gshare_pm * 1e-3, sitems, scta, gq0);
+  if (sitems.size() >= (1ull << 31)) return AR_ERR_ARG;
+  cudaError_t e = cudaSuccess;
+  if (sitems.size() > pl.sitems_cap) {
+    cudaFree(pl.d_sitems);
+    pl.d_sitems = nullptr;
+    pl.sitems_cap = 0;
+    e = cudaMalloc(&pl.d_sitems, sizeof(SItem) * sitems.size());
+    if (e == cudaSuccess) pl.sitems_cap = sitems.size();
+  }
+  if (e == cudaSuccess && scta.size() > pl.scta_cap) {
+    cudaFree(pl.d_scta);
+    pl.d_scta = nullptr;
+    pl.scta_cap = 0;
+    e = cudaMalloc(&pl.d_scta, sizeof(uint32_t) * scta.size());
+    if (e == cudaSuccess) pl.scta_cap = scta.size();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl.d_sitems, sitems.data(), sizeof(SItem) * sitems.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl.d_scta, scta.data(), sizeof(uint32_t) * scta.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    set_cuda_error(e);
+    return AR_ERR_CUDA;
+  }
+  pl.ns = (uint32_t)sitems.size();
+  pl.gq0 = gq0;
+  pl.grid = grid;
+  pl.shape = shape;
+  pl.gshare_pm = gshare_pm;
+  return AR_OK;
+}
+
+void free_plan(ar_plan* p) {
+  cudaFree(p->d_ritems);
+  cudaFree(p->d_rinfo);
+  cudaFree(p->d_sitems);
+  cudaFree(p->d_scta);
+  cudaFree(p->d_scratch);
+  delete p;
+}
+
+}  // namespace
 
 extern "C" int ar_plan_create(const int64_t* h_offsets, const int64_t* h_out_offsets, int64_t B,
                               ar_plan** out) {
   if (!out || B <= 0 || B >= (1ll << 31) || !h_offsets || !h_out_offsets) return AR_ERR_ARG;
   *out = nullptr;
   const DeviceInfo& dev = device_info();
-  const uint32_t grid = (uint32_t)std::max(1, dev.sm_count) * kCtasPerSm;
-  std::vector<double> cost(B);
-  double total_cost = 0.0;
+  auto* p = new ar_plan();
+  p->device = dev.device;
+  p->B = B;
+  p->off.assign(h_offsets, h_offsets + B + 1);
+  p->oo.assign(h_out_offsets, h_out_offsets + B + 1);
+  p->cost.resize(B);
   for (int64_t b = 0; b < B; ++b) {
     const int64_t M = h_offsets[b + 1] - h_offsets[b];
     const int64_t K = h_out_offsets[b + 1] - h_out_offsets[b];
-    if (M < 0 || K < 0 || M >= (1ll << 31) || K >= (1ll << 32)) return AR_ERR_ARG;
+    if (M < 0 || K < 0 || M >= (1ll << 31) || K >= (1ll << 32)) {
+      delete p;
+      return AR_ERR_ARG;
+    }
     // selections whose expected trial count grows like log M for spread-out
     // propensities, plus the first touch of the realization's lines
-    cost[b] = (double)K * (0.6 + std::log((double)std::max<int64_t>(M, 2))) + 0.05 * (double)M;
-    total_cost += cost[b];
+    p->cost[b] =
+        (double)K * (0.6 + std::log((double)std::max<int64_t>(M, 2))) + 0.05 * (double)M;
   }
   // reduction chunks: each realization cut into ceil(M / 1024) chunks of
   // equal length (a multiple of 4, so that only the realization's own ends
@@ -1015,71 +1141,15 @@ extern "C" int ar_plan_create(const int64_t* h_offsets, const int64_t* h_out_off
       e = nxt;
     } while (e < a1);
     rinfo[b].nch = (uint32_t)ritems.size() - rinfo[b].p0;
-    if (ritems.size() >= (1ull << 31)) return AR_ERR_ARG;
+    if (ritems.size() >= (1ull << 31)) {
+      delete p;
+      return AR_ERR_ARG;
+    }
   }
-  // Realizations by decreasing cost: the costliest go to home lists, longest
-  // processing time first onto the least loaded CTA, until the cost left is
-  // kGlobalShare of the total; the rest form the global queue in that order.
-  std::vector<int64_t> order(B);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int64_t x, int64_t y) { return cost[x] > cost[y]; });
-  using Load = std::pair<double, uint32_t>;
-  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-  for (uint32_t c = 0; c < grid; ++c) heap.push({0.0, c});
-  std::vector<std::vector<int64_t>> lists(grid);
-  double left = total_cost;
-  size_t n_home = 0;
-  for (; n_home < order.size() && left > kGlobalShare * total_cost; ++n_home) {
-    const int64_t b = order[n_home];
-    Load l = heap.top();
-    heap.pop();
-    lists[l.second].push_back(b);
-    l.first += cost[b];
-    heap.push(l);
-    left -= cost[b];
-  }
-  std::vector<SItem> sitems;
-  auto add_items = [&](int64_t b, uint32_t per) {
-    const uint32_t K = (uint32_t)(h_out_offsets[b + 1] - h_out_offsets[b]);
-    uint32_t s0 = 0;
-    do {  // one item even when K = 0
-      SItem s{};
-      s.a0 = h_offsets[b];
-      s.o0 = h_out_offsets[b];
-      s.M = (uint32_t)(h_offsets[b + 1] - h_offsets[b]);
-      s.b = (uint32_t)b;
-      s.s0 = s0;
-      s.s1 = (uint32_t)std::min<uint64_t>(K, (uint64_t)s0 + per);
-      sitems.push_back(s);
-      s0 = s.s1;
-    } while (s0 < K);
-  };
-  std::vector<uint32_t> scta(grid + 1, 0);
-  for (uint32_t c = 0; c < grid; ++c) {
-    for (int64_t b : lists[c]) add_items(b, kSItem);
-    scta[c + 1] = (uint32_t)sitems.size();
-  }
-  const uint32_t gq0 = (uint32_t)sitems.size();
-  for (size_t k = n_home; k < order.size(); ++k) add_items(order[k], kGItem);
-  if (sitems.size() >= (1ull << 31)) return AR_ERR_ARG;
-  auto* p = new ar_plan();
-  p->device = dev.device;
-  p->B = B;
   p->nr = (uint32_t)ritems.size();
-  p->ns = (uint32_t)sitems.size();
-  p->grid = grid;
-  p->gq0 = gq0;
-  p->d_ritems = nullptr;
-  p->d_rinfo = nullptr;
-  p->d_sitems = nullptr;
-  p->d_scta = nullptr;
-  p->d_scratch = nullptr;
   const size_t scratch_bytes = sizeof(Scratch) + sizeof(Part) * ritems.size();
   cudaError_t e = cudaMalloc(&p->d_ritems, sizeof(RItem) * ritems.size());
   if (e == cudaSuccess) e = cudaMalloc(&p->d_rinfo, sizeof(RInfo) * rinfo.size());
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_sitems, sizeof(SItem) * sitems.size());
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_scta, sizeof(uint32_t) * scta.size());
   if (e == cudaSuccess) e = cudaMalloc(&p->d_scratch, scratch_bytes);
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_ritems, ritems.data(), sizeof(RItem) * ritems.size(),
@@ -1087,21 +1157,16 @@ extern "C" int ar_plan_create(const int64_t* h_offsets, const int64_t* h_out_off
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_rinfo, rinfo.data(), sizeof(RInfo) * rinfo.size(),
                    cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(p->d_sitems, sitems.data(), sizeof(SItem) * sitems.size(),
-                   cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(p->d_scta, scta.data(), sizeof(uint32_t) * scta.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(p->d_scratch, 0, sizeof(Scratch));
   if (e != cudaSuccess) {
     set_cuda_error(e);
-    cudaFree(p->d_ritems);
-    cudaFree(p->d_rinfo);
-    cudaFree(p->d_sitems);
-    cudaFree(p->d_scta);
-    cudaFree(p->d_scratch);
-    delete p;
+    free_plan(p);
     return AR_ERR_CUDA;
+  }
+  const int rc = set_schedule(*p, 0, 300);  // default: 16 warps per CTA, 30 % global queue
+  if (rc) {
+    free_plan(p);
+    return rc;
   }
   *out = p;
   return AR_OK;
@@ -1111,14 +1176,10 @@ extern "C" void ar_plan_destroy(ar_plan* plan) {
   if (!plan) return;
   int cur = 0;
   cudaGetDevice(&cur);
-  if (cur != plan->device) cudaSetDevice(plan->device);
-  cudaFree(plan->d_ritems);
-  cudaFree(plan->d_rinfo);
-  cudaFree(plan->d_sitems);
-  cudaFree(plan->d_scta);
-  cudaFree(plan->d_scratch);
-  if (cur != plan->device) cudaSetDevice(cur);
-  delete plan;
+  const int pd = plan->device;
+  if (cur != pd) cudaSetDevice(pd);
+  free_plan(plan);
+  if (cur != pd) cudaSetDevice(cur);
 }
 
 extern "C" size_t ar_select_batched_workspace_size(int64_t B) {
@@ -1132,7 +1193,7 @@ namespace {
 int batched_params(const void* d_alpha_cat, int dtype, const int64_t* d_offsets,
                    const int64_t* d_out_offsets, int64_t B, const ar_plan* plan,
                    uint32_t* d_status, void* d_work, size_t work_bytes, Params& p,
-                   uint32_t& sel_grid, bool& stream_path) {
+                   uint32_t& sel_grid, int& shape, bool& stream_path) {
   if (!valid_dtype(dtype) || B < 0 || B >= (1ll << 31)) return AR_ERR_ARG;
   if (!d_alpha_cat || !d_offsets || !d_status) return AR_ERR_ARG;
   if (!aligned(d_alpha_cat, dtype_size(dtype)) || !aligned(d_offsets, 8) ||
@@ -1140,6 +1201,7 @@ int batched_params(const void* d_alpha_cat, int dtype, const int64_t* d_offsets,
     return AR_ERR_ALIGN;
   p = Params{};
   sel_grid = 0;
+  shape = 0;
   stream_path = false;
   p.vec_ok = aligned(d_alpha_cat, 16) ? 1u : 0u;
   if (plan) {
@@ -1156,6 +1218,7 @@ int batched_params(const void* d_alpha_cat, int dtype, const int64_t* d_offsets,
     p.scratch = reinterpret_cast<Scratch*>(plan->d_scratch);
     p.parts = reinterpret_cast<Part*>(plan->d_scratch + sizeof(Scratch));
     sel_grid = plan->grid;
+    shape = plan->shape;
     stream_path = dtype == AR_F32 && p.vec_ok;
   } else {
     if (!d_work || work_bytes < ar_select_batched_workspace_size(B)) return AR_ERR_WORKSPACE;
@@ -1189,12 +1252,13 @@ int selection_params(uint64_t seed, uint64_t sel_offset, uint32_t realization_ba
   return AR_OK;
 }
 
-int dispatch_select(int dtype, int cmp, const Params& p, uint32_t sel_grid, cudaStream_t s) {
+int dispatch_select(int dtype, int cmp, const Params& p, uint32_t sel_grid, int shape,
+                    cudaStream_t s) {
   if (dtype == AR_F32)
-    return cmp == AR_CMP_F32 ? launch_select<float, AR_CMP_F32>(p, sel_grid, s)
-                             : launch_select<float, AR_CMP_F64>(p, sel_grid, s);
-  return cmp == AR_CMP_F32 ? launch_select<double, AR_CMP_F32>(p, sel_grid, s)
-                           : launch_select<double, AR_CMP_F64>(p, sel_grid, s);
+    return cmp == AR_CMP_F32 ? launch_select<float, AR_CMP_F32>(p, sel_grid, shape, s)
+                             : launch_select<float, AR_CMP_F64>(p, sel_grid, shape, s);
+  return cmp == AR_CMP_F32 ? launch_select<double, AR_CMP_F32>(p, sel_grid, shape, s)
+                           : launch_select<double, AR_CMP_F64>(p, sel_grid, shape, s);
 }
 
 }  // namespace
@@ -1206,9 +1270,10 @@ extern "C" int ar_bound_batched(const void* d_alpha_cat, int dtype, const int64_
   if (B == 0 && valid_dtype(dtype)) return AR_OK;
   Params p;
   uint32_t sel_grid;
+  int shape;
   bool stream_path;
   int rc = batched_params(d_alpha_cat, dtype, d_offsets, d_offsets, B, plan, d_status, d_work,
-                          work_bytes, p, sel_grid, stream_path);
+                          work_bytes, p, sel_grid, shape, stream_path);
   if (rc) return rc;
   if (!d_bound_sum) return AR_ERR_ARG;
   if (!aligned(d_bound_sum, 8)) return AR_ERR_ALIGN;
@@ -1230,9 +1295,10 @@ extern "C" int ar_select_batched_bounded(const void* d_alpha_cat, int dtype,
   if (B == 0 && valid_dtype(dtype) && valid_cmp(cmp)) return AR_OK;
   Params p;
   uint32_t sel_grid;
+  int shape;
   bool stream_path;
   int rc = batched_params(d_alpha_cat, dtype, d_offsets, d_out_offsets, B, plan, d_status,
-                          d_work, work_bytes, p, sel_grid, stream_path);
+                          d_work, work_bytes, p, sel_grid, shape, stream_path);
   if (rc) return rc;
   rc = selection_params(seed, sel_offset, realization_base, cmp, trial_cap, B, d_out_offsets,
                         d_idx, d_stats, p);
@@ -1242,7 +1308,7 @@ extern "C" int ar_select_batched_bounded(const void* d_alpha_cat, int dtype,
   p.bound_in = d_bound;
   p.bound_stride = bound_stride;
   p.bound_given = 1u;
-  return dispatch_select(dtype, cmp, p, sel_grid, static_cast<cudaStream_t>(stream));
+  return dispatch_select(dtype, cmp, p, sel_grid, shape, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64_t* d_offsets,
@@ -1254,9 +1320,10 @@ extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64
   if (B == 0 && valid_dtype(dtype) && valid_cmp(cmp)) return AR_OK;
   Params p;
   uint32_t sel_grid;
+  int shape;
   bool stream_path;
   int rc = batched_params(d_alpha_cat, dtype, d_offsets, d_out_offsets, B, plan, d_status,
-                          d_work, work_bytes, p, sel_grid, stream_path);
+                          d_work, work_bytes, p, sel_grid, shape, stream_path);
   if (rc) return rc;
   rc = selection_params(seed, sel_offset, realization_base, cmp, trial_cap, B, d_out_offsets,
                         d_idx, d_stats, p);
@@ -1270,5 +1337,66 @@ extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64
   rc = dtype == AR_F32 ? launch_bound<float>(p, stream_path, s)
                        : launch_bound<double>(p, stream_path, s);
   if (rc) return rc;
-  return dispatch_select(dtype, cmp, p, sel_grid, s);
+  return dispatch_select(dtype, cmp, p, sel_grid, shape, s);
+}
+
+extern "C" int ar_plan_autotune(ar_plan* plan, const void* d_alpha_cat, int dtype,
+                                const int64_t* d_offsets, const int64_t* d_out_offsets,
+                                uint64_t seed, int cmp, double* d_bound_sum, int32_t* d_idx,
+                                ar_stats* d_stats, uint32_t* d_status, int reps,
+                                int32_t* h_choice, void* stream) {
+  if (!plan || reps < 1 || reps > 10000) return AR_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int shares[3] = {0, 300, 600};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  if (ce != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    set_cuda_error(ce);
+    return AR_ERR_CUDA;
+  }
+  int best_shape = plan->shape, best_share = plan->gshare_pm, rc = AR_OK;
+  float best_ms = 0.f;
+  bool have = false;
+  for (int sh = 0; sh < 3 && rc == AR_OK; ++sh) {
+    for (int g = 0; g < 3 && rc == AR_OK; ++g) {
+      rc = set_schedule(*plan, sh, shares[g]);
+      if (rc) break;
+      auto call = [&]() {
+        return ar_select_batched(d_alpha_cat, dtype, d_offsets, d_out_offsets, plan->B, seed, 0,
+                                 0, cmp, 1ull << 20, plan, d_bound_sum, d_idx, d_stats, d_status,
+                                 nullptr, 0, stream);
+      };
+      for (int w = 0; w < 2 && rc == AR_OK; ++w) rc = call();
+      if (rc) break;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < reps && rc == AR_OK; ++r) rc = call();
+      cudaEventRecord(e1, s);
+      ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) {
+        set_cuda_error(ce);
+        rc = AR_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (!have || ms < best_ms) {
+        have = true;
+        best_ms = ms;
+        best_shape = sh;
+        best_share = shares[g];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const int rc2 = set_schedule(*plan, best_shape, best_share);
+  if (rc == AR_OK) rc = rc2;
+  if (rc == AR_OK && h_choice) {
+    h_choice[0] = kSelShapes[best_shape];
+    h_choice[1] = best_share;
+    h_choice[2] = (int32_t)(best_ms * 1e6f / (float)reps);  // ns per call
+  }
+  return rc;
 }

@@ -321,3 +321,22 @@ def test_batched_invalid_realization(gb, orc, plan):
     np.testing.assert_array_equal(np.isnan(g), np.isnan(obs))
     np.testing.assert_array_equal(g[~np.isnan(g[:, 0]), 0], obs[~np.isnan(obs[:, 0]), 0])
     assert int(st.item()) == ost == gb.AR_STATUS_BAD_ALPHA
+
+
+def test_plan_autotune(gb, orc):
+    """The autotuner times the tile candidates on the data and keeps one;
+    results do not depend on the schedule."""
+    import torch
+    bt = W.batched_uneven(B=600, seed=306, K=64)
+    a, off, oo = _t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets)
+    plan = gb.Plan(bt.offsets, bt.out_offsets)
+    bs = torch.empty((bt.B, 2), dtype=torch.float64, device="cuda")
+    idx = torch.empty(int(bt.out_offsets[-1]), dtype=torch.int32, device="cuda")
+    stats = torch.zeros(3, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    warps, share, ns = gb.ar_plan_autotune(plan, a, off, oo, 1, 0, bs, idx, stats, st, reps=3)
+    assert warps in (8, 16, 32) and share in (0, 300, 600) and ns > 0
+    _, oidx, ostats, _ = orc.select_batched(bt, nthreads=8)
+    _, idx2, stats2, st2 = gb.select_batched(a, off, oo, plan=plan)
+    np.testing.assert_array_equal(idx2.cpu().numpy(), oidx)
+    np.testing.assert_array_equal(stats2.cpu().numpy().astype(np.uint64), ostats)
