@@ -627,9 +627,19 @@ def main():
             times.append(s0e.elapsed_time(s1e))
         steps_done = int(sx["step"].sum().item())
         ms = float(np.median(times))
+        trials_ssa = float(sx["trials"].sum().item())
+        sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+        clk = float(measured_peaks()[2].get("sm_max_mhz", 2070.0))
+        alu_peak = IMAD_PER_SM_CLK * sm_count * clk * 1e6 / PHILOX_IMAD_PER_BLOCK
         ssa = {"value": steps_done / (ms * 1e-3), "unit": "SSA steps/s",
                "selections_per_s": steps_done / (ms * 1e-3), "kernel_ms": ms,
-               "trials_per_step": float(sx["trials"].sum().item()) / max(steps_done, 1),
+               "trials_per_step": trials_ssa / max(steps_done, 1),
+               "roofline": {"bound": "alu", "kernel": "k_ssa<AR_CMP_F32>",
+                            "achieved": trials_ssa / 2.0 / (ms * 1e-3), "peak": alu_peak,
+                            "unit": "Philox4x32-10 blocks/s",
+                            "frac": trials_ssa / 2.0 / (ms * 1e-3) / alu_peak,
+                            "traffic": profiled_traffic("k_ssa_network_641x1029.md"),
+                            "note": "sequential per realization; issue-bound (see profile)"},
                "status_or": int(np.bitwise_or.reduce(sx["status"].cpu().numpy())),
                "workload": f"{B_ssa} realizations of a random mass-action network "
                            f"(641 species, 1029 uni/bi/dimer reactions, seed 500), "
