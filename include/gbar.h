@@ -67,6 +67,7 @@ extern "C" {
 #define AR_STATUS_ABSORBED 16u  /* SSA realization reached a0 = 0          */
 #define AR_STATUS_TIMEOUT 32u   /* a bounded device wait gave up           */
 #define AR_STATUS_UNSUPPORTED 64u /* a batched realization with M_b >= 2^31 */
+#define AR_STATUS_T_END 128u      /* SSA realization reached its time limit    */
 
 typedef enum { AR_F32 = 0, AR_F64 = 1 } ar_dtype;
 typedef enum { AR_CMP_F32 = 0, AR_CMP_F64 = 1 } ar_cmp;
@@ -383,6 +384,32 @@ int ssa_step_batched(const ssa_net *net, int64_t B, int32_t *d_X, double *d_a, d
                      uint64_t *d_step, int64_t nsteps, uint64_t seed, uint32_t realization_base,
                      int cmp, uint64_t trial_cap, int32_t *d_last, uint32_t *d_status,
                      uint64_t *d_trials, void *stream);
+
+/* ---------------------------------------------------------------------
+ * ssa_run_until -- advances B realizations to the time limit t_end (the
+ * SSA loop of Section "The Stochastic Simulation Algorithm": repeat until
+ * the simulated time passes the end), at most max_steps reactions per
+ * realization and call, recording trajectory samples.  Each step first
+ * draws its waiting time tau (same stream as ssa_step_batched); if
+ * t + tau > t_end the reaction does not fire and AR_STATUS_T_END is set
+ * (informational); t stays at the realization's last reaction, its state
+ * holding on [t, t_end], so a later call with a larger t_end continues
+ * exactly as a single call would.  An absorbed realization (a_0 = 0)
+ * keeps its state to t_end.
+ *   d_sample_times  [nsamp] ascending sample times (nullable when nsamp =
+ *                   0).  d_traj[b][k][s] receives the count of species
+ *                   d_sample_species[s] (nullable: species s) at time
+ *                   t_k, i.e. after the last reaction at a time <= t_k, for
+ *                   every t_k this call passes (t_k >= the realization's
+ *                   time at the start of the call and <= where it stops).
+ *   Other arguments as in ssa_step_batched.
+ * ------------------------------------------------------------------- */
+int ssa_run_until(const ssa_net *net, int64_t B, int32_t *d_X, double *d_a, double *d_t,
+                  uint64_t *d_step, double t_end, int64_t max_steps, uint64_t seed,
+                  uint32_t realization_base, int cmp, uint64_t trial_cap,
+                  const double *d_sample_times, int32_t nsamp, const int32_t *d_sample_species,
+                  int32_t nspec, int32_t *d_traj, int32_t *d_last, uint32_t *d_status,
+                  uint64_t *d_trials, void *stream);
 
 #ifdef __cplusplus
 }

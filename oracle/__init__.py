@@ -72,6 +72,10 @@ def lib():
         L.orc_ssa.argtypes = [ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, vp, i64,
                               vp, vp, vp, i64, u64, u32, i32, u64, vp, vp, vp, vp, i32]
         L.orc_ssa.restype = None
+        L.orc_ssa_until.argtypes = [ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, vp, i64,
+                                    vp, vp, vp, ctypes.c_double, i64, u64, u32, i32, u64, vp,
+                                    i32, vp, i32, vp, vp, vp, vp, i32]
+        L.orc_ssa_until.restype = None
         L.orc_num_threads_available.restype = i32
         _lib = L
     return _lib
@@ -203,3 +207,36 @@ def ssa(net, X, t=None, step=None, nsteps=1, seed=1, realization_base=0, cmp=CMP
     if want_a:
         out["a"] = a_out
     return out
+
+
+ST_T_END = 128
+
+
+def ssa_until(net, X, t_end, t=None, step=None, max_steps=1 << 40, seed=1, realization_base=0,
+              cmp=CMP_F64, trial_cap=1 << 20, status=None, sample_times=None, species=None,
+              nthreads=1):
+    """Run B realizations to the time limit t_end with trajectory samples.
+
+    -> dict(X, t, step, last, status, trials, traj [B, nsamp, nspec])."""
+    X = np.array(X, dtype=np.int32, order="C", copy=True)
+    B = X.shape[0]
+    t = np.zeros(B, dtype=np.float64) if t is None else np.array(t, dtype=np.float64)
+    step = (np.zeros(B, dtype=np.uint64) if step is None
+            else np.array(step, dtype=np.uint64))
+    status = (np.zeros(B, dtype=np.uint32) if status is None
+              else np.array(status, dtype=np.uint32))
+    last = -np.ones(B, dtype=np.int32)
+    trials = np.zeros(B, dtype=np.uint64)
+    st_times = (np.zeros(0) if sample_times is None
+                else np.ascontiguousarray(sample_times, dtype=np.float64))
+    sp = None if species is None else np.ascontiguousarray(species, dtype=np.int32)
+    nspec = net.n_species if sp is None else sp.size
+    traj = np.full((B, st_times.size, nspec), -1, dtype=np.int32)
+    arrs = [np.ascontiguousarray(x) for x in (net.rtype, net.reactants, net.rate, net.nu_ptr,
+                                              net.nu_species, net.nu_delta)]
+    lib().orc_ssa_until(net.n_species, net.M, *[_ptr(x) for x in arrs], B, _ptr(X), _ptr(t),
+                        _ptr(step), float(t_end), max_steps, ctypes.c_uint64(seed),
+                        realization_base, cmp, ctypes.c_uint64(trial_cap), _ptr(st_times),
+                        st_times.size, _ptr(sp), nspec, _ptr(traj), _ptr(last), _ptr(status),
+                        _ptr(trials), nthreads)
+    return dict(X=X, t=t, step=step, last=last, status=status, trials=trials, traj=traj)

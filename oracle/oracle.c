@@ -470,6 +470,80 @@ void orc_ssa(int32_t N, int32_t M, const int32_t *rtype, const int32_t *reac,
     }
 }
 
+/* SSA to a time limit (the loop of Section "The Stochastic Simulation     */
+/* Algorithm" run until the simulated time passes t_end), with trajectory   */
+/* samples.  Each step draws its waiting time first; if t + tau > t_end the */
+/* reaction does not fire and status T_END (128) is set; t stays at the     */
+/* last reaction (the state holds on [t, t_end]), so a later call with a    */
+/* larger limit continues exactly as one call would.                       */
+/* Sample k (times ascending) records the state after the last reaction at  */
+/* a time <= t_k, for the t_k this call passes; an absorbed realization     */
+/* keeps its state to t_end.  At most max_steps reactions per realization.  */
+void orc_ssa_until(int32_t N, int32_t M, const int32_t *rtype, const int32_t *reac,
+                   const double *rate, const int32_t *nu_ptr, const int32_t *nu_sp,
+                   const int32_t *nu_d, int64_t B, int32_t *X, double *t, uint64_t *step,
+                   double t_end, int64_t max_steps, uint64_t seed, uint32_t realization_base,
+                   int cmp, uint64_t trial_cap, const double *samp_t, int32_t nsamp,
+                   const int32_t *samp_sp, int32_t nspec, int32_t *traj, int32_t *last,
+                   uint32_t *status, uint64_t *trials_out, int nthreads)
+{
+    (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+    for (int64_t b = 0; b < B; b++) {
+        int32_t *Xb = X + b * (int64_t)N;
+        double a[M > 0 ? M : 1];
+        uint32_t bid = realization_base + (uint32_t)b;
+        uint64_t ntr = 0;
+        int32_t k = 0;
+        while (k < nsamp && samp_t[k] < t[b]) k++;
+        for (int64_t n = 0; n < max_steps; n++) {
+            if (status[b] & (ST_ABSORBED | ST_TRIAL_CAP | ST_BAD_ALPHA)) break;
+            double T = 0.0, a0 = 0.0;
+            for (int32_t r = 0; r < M; r++) {
+                a[r] = propensity(rtype[r], reac + 2 * r, rate[r], Xb);
+                if (!(a[r] >= 0.0) || isinf(a[r])) status[b] |= ST_BAD_ALPHA;
+                if (a[r] > T) T = a[r];
+                a0 += a[r];
+            }
+            if (status[b] & ST_BAD_ALPHA) break;
+            if (T == 0.0) {
+                status[b] |= ST_ABSORBED;
+                for (; k < nsamp && samp_t[k] <= t_end; k++)
+                    for (int32_t q = 0; q < nspec; q++)
+                        traj[(b * nsamp + k) * (int64_t)nspec + q] = Xb[samp_sp ? samp_sp[q] : q];
+                break;
+            }
+            uint32_t s = (uint32_t)step[b];
+            uint32_t ctr[4] = {0u, s, bid, 1u};
+            uint32_t w[4];
+            orc_philox4x32_10(ctr, seed, w);
+            double t_next = t[b] + -log(1.0 - u53(w[0], w[1])) / a0;
+            int over = t_next > t_end;
+            for (; k < nsamp && (over ? samp_t[k] <= t_end : samp_t[k] < t_next); k++)
+                for (int32_t q = 0; q < nspec; q++)
+                    traj[(b * nsamp + k) * (int64_t)nspec + q] = Xb[samp_sp ? samp_sp[q] : q];
+            if (over) {
+                status[b] |= 128u;
+                break;
+            }
+            uint64_t nt = 0;
+            int64_t j = select_one(a, 1, M, T, cmp, seed, s, bid, trial_cap, &nt);
+            ntr += nt;
+            if (j >= M) {
+                status[b] |= ST_TRIAL_CAP;
+                break;
+            }
+            for (int32_t q = nu_ptr[j]; q < nu_ptr[j + 1]; q++) Xb[nu_sp[q]] += nu_d[q];
+            t[b] = t_next;
+            step[b] += 1;
+            if (last) last[b] = (int32_t)j;
+        }
+        if (trials_out) trials_out[b] += ntr;
+    }
+}
+
 int orc_num_threads_available(void)
 {
 #ifdef _OPENMP

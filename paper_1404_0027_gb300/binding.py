@@ -63,6 +63,9 @@ SIGNATURES = {
     "ssa_step_batched": (_int, [_vp, _i64, _vp, _vp, _vp, _vp, _i64, _u64, _u32, _int, _u64,
                                 _vp, _vp, _vp, _vp]),
     "ar_plan_destroy": (None, [_vp]),
+    "ssa_run_until": (_int, [_vp, _i64, _vp, _vp, _vp, _vp, ctypes.c_double, _i64, _u64, _u32,
+                             _int, _u64, _vp, ctypes.c_int32, _vp, ctypes.c_int32, _vp, _vp,
+                             _vp, _vp, _vp]),
     "ar_select_batched": (_int, [_vp, _int, _vp, _vp, _i64, _u64, _u64, _u32, _int, _u64, _vp,
                                  _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "ar_bound_batched": (_int, [_vp, _int, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
@@ -450,4 +453,52 @@ def ssa_run(net, X0, nsteps, seed=1, realization_base=0, cmp=AR_CMP_F32, trial_c
     ssa_step_batched(net, out["X"], out["a"], out["t"], out["step"], nsteps, seed,
                      realization_base, cmp, trial_cap, out["last"], out["status"],
                      out["trials"], stream)
+    return out
+
+
+def ssa_run_until(net, X, a, t, step, t_end, max_steps, seed, realization_base, cmp, trial_cap,
+                  sample_times, species, traj, last, status, trials, stream=None):
+    """As ssa_step_batched, to the time limit t_end, recording traj[b, k, s] =
+    count of species[s] at sample_times[k] (CUDA tensors; sample_times and
+    traj may be None)."""
+    B = X.shape[0]
+    nsamp = 0 if sample_times is None else sample_times.numel()
+    nspec = 0 if nsamp == 0 else (net.N if species is None else species.numel())
+    _check(lib().ssa_run_until(
+        ctypes.c_void_p(net.handle), B, _dev(X, torch.int32, "X"), _dev(a, torch.float64, "a"),
+        _dev(t, torch.float64, "t"), _dev(step, torch.int64, "step"), float(t_end), max_steps,
+        seed, realization_base, cmp, trial_cap, _dev(sample_times, torch.float64, "sample_times"),
+        nsamp, _dev(species, torch.int32, "species"), nspec, _dev(traj, torch.int32, "traj"),
+        _dev(last, torch.int32, "last"), _dev(status, torch.int32, "status"),
+        _dev(trials, torch.int64, "trials"), _stream(stream)), "ssa_run_until")
+
+
+def ssa_until(net, X0, t_end, sample_times=None, species=None, max_steps=1 << 40, seed=1,
+              realization_base=0, cmp=AR_CMP_F32, trial_cap=1 << 20, t=None, step=None,
+              stream=None):
+    """Convenience: runs to t_end with samples -> dict of CUDA tensors
+    X, a, t, step, last, status, trials, traj [B, nsamp, nspec]."""
+    import numpy as np
+    dev = torch.device("cuda")
+    Xd = torch.as_tensor(np.ascontiguousarray(X0, dtype=np.int32)).to(dev).contiguous()
+    B = Xd.shape[0]
+    ts = None if sample_times is None else torch.as_tensor(
+        np.asarray(sample_times, dtype=np.float64)).to(dev).contiguous()
+    sp = None if species is None else torch.as_tensor(
+        np.asarray(species, dtype=np.int32)).to(dev).contiguous()
+    nspec = net.N if sp is None else sp.numel()
+    nsamp = 0 if ts is None else ts.numel()
+    out = dict(
+        X=Xd, a=torch.zeros((B, net.M), dtype=torch.float64, device=dev),
+        t=(torch.zeros(B, dtype=torch.float64, device=dev) if t is None
+           else torch.as_tensor(t, dtype=torch.float64).to(dev).contiguous()),
+        step=(torch.zeros(B, dtype=torch.int64, device=dev) if step is None
+              else torch.as_tensor(np.asarray(step).astype(np.int64)).to(dev).contiguous()),
+        last=-torch.ones(B, dtype=torch.int32, device=dev),
+        status=torch.zeros(B, dtype=torch.int32, device=dev),
+        trials=torch.zeros(B, dtype=torch.int64, device=dev),
+        traj=torch.full((B, nsamp, nspec), -1, dtype=torch.int32, device=dev))
+    ssa_run_until(net, out["X"], out["a"], out["t"], out["step"], t_end, max_steps, seed,
+                  realization_base, cmp, trial_cap, ts, sp, out["traj"] if nsamp else None,
+                  out["last"], out["status"], out["trials"], stream)
     return out

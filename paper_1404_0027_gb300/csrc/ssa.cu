@@ -67,6 +67,13 @@ struct SsaParams {
   uint32_t b_base;
   uint32_t k0, k1;
   uint32_t smem_stride;  // bytes of shared memory per warp
+  // run to a time limit, with trajectory samples (ssa_run_until)
+  double t_end;
+  const double* samp_t;   // [nsamp] ascending sample times
+  int32_t nsamp;
+  const int32_t* samp_sp; // [nspec] species recorded (NULL: 0 .. nspec-1)
+  int32_t nspec;
+  int32_t* traj;          // [B][nsamp][nspec]
 };
 
 // Mass-action propensity: one FP64 rounding of c times the exact count h.
@@ -150,7 +157,7 @@ __device__ __forceinline__ double unfix128(I128 x, int S) {
   return ldexp(v, -S);
 }
 
-template <int CMP>
+template <int CMP, bool TIMED>
 __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t lane = threadIdx.x & 31u;
@@ -205,6 +212,17 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
   double E = 0.0;
   I128 a0_lane{0ull, 0ull};
   int blk_fill = 32;  // force a refill before the first step
+  // trajectory samples: the state at sample time t_k is the state after the
+  // last reaction at a time <= t_k
+  int ks = 0;
+  if constexpr (TIMED)
+    while (ks < p.nsamp && p.samp_t[ks] < t) ++ks;
+  auto record_until = [&](double lim, bool inclusive) {
+    for (; ks < p.nsamp && (inclusive ? p.samp_t[ks] <= lim : p.samp_t[ks] < lim); ++ks) {
+      int32_t* dst = p.traj + ((size_t)b * (size_t)p.nsamp + (size_t)ks) * (size_t)p.nspec;
+      for (int q = (int)lane; q < p.nspec; q += 32) dst[q] = X[p.samp_sp ? p.samp_sp[q] : q];
+    }
+  };
 
   auto flush_block = [&](int used) {
     // tau_i = E_i / a0_i for the used steps (lane-parallel FP64), added to t
@@ -220,7 +238,7 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
 
   for (long long n = 0; n < p.nsteps; ++n) {
     if (blk_fill == 32) {
-      if (n > 0) flush_block(32);
+      if (n > 0 && !TIMED) flush_block(32);
       // exponential variates of the next 32 steps: -ln(1 - u53), u53 from
       // counter (0, step, b, 1), words 0 and 1
       const uint4 w = philox10(make_uint4(0u, (uint32_t)(step + lane), bid, 1u), p.k0, p.k1);
@@ -241,7 +259,20 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
     }
     if (T == 0.0) {
       st |= AR_STATUS_ABSORBED;
+      if (TIMED) record_until(p.t_end, true);  // the state holds to t_end
       break;
+    }
+    double t_next = 0.0;
+    if (TIMED) {
+      // this step's waiting time first: a reaction after t_end does not fire
+      const double tau = __ddiv_rn(__shfl_sync(kFull, E, blk_fill), unfix128(a0x, S));
+      t_next = __dadd_rn(t, tau);
+      if (t_next > p.t_end) {  // t stays at the last reaction: a resumed run is exact
+        record_until(p.t_end, true);
+        st |= AR_STATUS_T_END;
+        break;
+      }
+      record_until(t_next, false);
     }
     // ---- AR selection: the whole warp tests trials 64 at a time
     const uint32_t M32 = (uint32_t)M;
@@ -348,9 +379,10 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
     }
     ++step;
     last = j;
+    if (TIMED) t = t_next;
   }
   // waiting times of the steps of the last, partial block
-  if (blk_fill > 0 && blk_fill <= 32) flush_block(blk_fill);
+  if (!TIMED && blk_fill > 0 && blk_fill <= 32) flush_block(blk_fill);
   if (ovf) st |= AR_STATUS_UNSUPPORTED;
   if (lane == 0) {
     p.t[b] = t;
@@ -468,11 +500,12 @@ extern "C" void ssa_net_destroy(ssa_net* n) {
   delete n;
 }
 
-extern "C" int ssa_step_batched(const ssa_net* net, int64_t B, int32_t* d_X, double* d_a,
-                                double* d_t, uint64_t* d_step, int64_t nsteps, uint64_t seed,
-                                uint32_t realization_base, int cmp, uint64_t trial_cap,
-                                int32_t* d_last, uint32_t* d_status, uint64_t* d_trials,
-                                void* stream) {
+namespace {
+
+int ssa_launch(const ssa_net* net, int64_t B, int32_t* d_X, double* d_a, double* d_t,
+               uint64_t* d_step, int64_t nsteps, uint64_t seed, uint32_t realization_base,
+               int cmp, uint64_t trial_cap, int32_t* d_last, uint32_t* d_status,
+               uint64_t* d_trials, SsaParams p, bool timed, void* stream) {
   if (!net || B < 0 || B >= (1ll << 31) || nsteps < 0 || !valid_cmp(cmp)) return AR_ERR_ARG;
   if (trial_cap < 1 || trial_cap > (1ull << 32)) return AR_ERR_ARG;
   if (B == 0 || nsteps == 0) return AR_OK;
@@ -487,7 +520,6 @@ extern "C" int ssa_step_batched(const ssa_net* net, int64_t B, int32_t* d_X, dou
   const DeviceInfo& dev = device_info();
   if ((int)smem > (dev.max_smem_optin > 0 ? dev.max_smem_optin : 227 * 1024))
     return AR_ERR_UNSUPPORTED;
-  SsaParams p{};
   p.rtype = net->d_rtype;
   p.reac = net->d_reac;
   p.rate = net->d_rate;
@@ -513,12 +545,51 @@ extern "C" int ssa_step_batched(const ssa_net* net, int64_t B, int32_t* d_X, dou
   p.smem_stride = stride;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const unsigned grid = (unsigned)((B + kWarpsS - 1) / kWarpsS);
+  auto go = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kern<<<grid, kNTS, smem, s>>>(p);
+  };
   if (cmp == AR_CMP_F32) {
-    cudaFuncSetAttribute(k_ssa<AR_CMP_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ssa<AR_CMP_F32><<<grid, kNTS, smem, s>>>(p);
+    if (timed) go(k_ssa<AR_CMP_F32, true>);
+    else go(k_ssa<AR_CMP_F32, false>);
   } else {
-    cudaFuncSetAttribute(k_ssa<AR_CMP_F64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ssa<AR_CMP_F64><<<grid, kNTS, smem, s>>>(p);
+    if (timed) go(k_ssa<AR_CMP_F64, true>);
+    else go(k_ssa<AR_CMP_F64, false>);
   }
   return check_launch();
+}
+
+}  // namespace
+
+extern "C" int ssa_step_batched(const ssa_net* net, int64_t B, int32_t* d_X, double* d_a,
+                                double* d_t, uint64_t* d_step, int64_t nsteps, uint64_t seed,
+                                uint32_t realization_base, int cmp, uint64_t trial_cap,
+                                int32_t* d_last, uint32_t* d_status, uint64_t* d_trials,
+                                void* stream) {
+  SsaParams p{};
+  return ssa_launch(net, B, d_X, d_a, d_t, d_step, nsteps, seed, realization_base, cmp,
+                    trial_cap, d_last, d_status, d_trials, p, false, stream);
+}
+
+extern "C" int ssa_run_until(const ssa_net* net, int64_t B, int32_t* d_X, double* d_a,
+                             double* d_t, uint64_t* d_step, double t_end, int64_t max_steps,
+                             uint64_t seed, uint32_t realization_base, int cmp,
+                             uint64_t trial_cap, const double* d_sample_times, int32_t nsamp,
+                             const int32_t* d_sample_species, int32_t nspec, int32_t* d_traj,
+                             int32_t* d_last, uint32_t* d_status, uint64_t* d_trials,
+                             void* stream) {
+  if (!(t_end >= 0.0) || nsamp < 0 || nspec < 0) return AR_ERR_ARG;
+  if (nsamp > 0 && (!d_sample_times || !d_traj || nspec <= 0)) return AR_ERR_ARG;
+  if (!net || (!d_sample_species && nspec > net->N)) return AR_ERR_ARG;
+  if (!aligned(d_sample_times, 8) || !aligned(d_sample_species, 4) || !aligned(d_traj, 4))
+    return AR_ERR_ALIGN;
+  SsaParams p{};
+  p.t_end = t_end;
+  p.samp_t = d_sample_times;
+  p.nsamp = nsamp;
+  p.samp_sp = d_sample_species;
+  p.nspec = nsamp > 0 ? nspec : 0;
+  p.traj = d_traj;
+  return ssa_launch(net, B, d_X, d_a, d_t, d_step, max_steps, seed, realization_base, cmp,
+                    trial_cap, d_last, d_status, d_trials, p, true, stream);
 }

@@ -92,3 +92,51 @@ def test_ssa_birth_death_and_trial_cap(gb, orc):
     o = orc.ssa(net, X0, nsteps=50, trial_cap=1)
     np.testing.assert_array_equal(g["status"].cpu().numpy().astype(np.uint32), o["status"])
     np.testing.assert_array_equal(g["X"].cpu().numpy(), o["X"])
+
+
+@pytest.mark.parametrize("cmp", [0, 1])
+def test_ssa_until_parity(gb, orc, cmp):
+    """Time-limited runs with trajectory samples: counts, samples, steps,
+    status, last reaction and trials bit-exact against the oracle."""
+    net = W.random_network(N=40, M=70, seed=8)
+    X0 = W.initial_counts(40, 64, seed=9)
+    ts = np.linspace(0.0, 0.02, 9)
+    sp = np.array([0, 5, 17, 39], dtype=np.int32)
+    gn = gb.SsaNet(net)
+    g = gb.ssa_until(gn, X0, 0.02, sample_times=ts, species=sp, cmp=cmp, seed=4)
+    o = orc.ssa_until(net, X0, 0.02, sample_times=ts, species=sp, cmp=cmp, seed=4, nthreads=8)
+    np.testing.assert_array_equal(g["X"].cpu().numpy(), o["X"])
+    np.testing.assert_array_equal(g["traj"].cpu().numpy(), o["traj"])
+    np.testing.assert_array_equal(g["step"].cpu().numpy().astype(np.uint64), o["step"])
+    np.testing.assert_array_equal(g["status"].cpu().numpy().astype(np.uint32), o["status"])
+    np.testing.assert_array_equal(g["last"].cpu().numpy(), o["last"])
+    np.testing.assert_array_equal(g["trials"].cpu().numpy().astype(np.uint64), o["trials"])
+    assert (o["status"] == orc.ST_T_END).all()
+    rtol = float(o["step"].max()) * 4e-16 + 1e-13
+    np.testing.assert_allclose(g["t"].cpu().numpy(), o["t"], rtol=rtol, atol=0)
+    gn.close()
+
+
+def test_ssa_until_absorption_and_resume(gb, orc):
+    """Absorbed realizations hold their state to the limit; two calls split
+    at an intermediate limit give the single call's path."""
+    net = W.network_from_lists(1, [(W.RT_UNI, (0, -1), 1.0, [(0, -1)])])
+    X0 = np.full((96, 1), 5, dtype=np.int32)
+    ts = np.linspace(0.0, 50.0, 11)
+    gn = gb.SsaNet(net)
+    g = gb.ssa_until(gn, X0, 50.0, sample_times=ts, cmp=1)
+    o = orc.ssa_until(net, X0, 50.0, sample_times=ts, cmp=1)
+    np.testing.assert_array_equal(g["traj"].cpu().numpy(), o["traj"])
+    np.testing.assert_array_equal(g["status"].cpu().numpy().astype(np.uint32), o["status"])
+    gn.close()
+    net2 = W.random_network(N=30, M=50, seed=12)
+    X1 = W.initial_counts(30, 40, seed=13)
+    gn2 = gb.SsaNet(net2)
+    full = gb.ssa_until(gn2, X1, 0.05, seed=5)
+    h = gb.ssa_until(gn2, X1, 0.02, seed=5)
+    r = gb.ssa_until(gn2, h["X"].cpu().numpy(), 0.05, seed=5, t=h["t"].cpu().numpy(),
+                     step=h["step"].cpu().numpy())
+    np.testing.assert_array_equal(r["X"].cpu().numpy(), full["X"].cpu().numpy())
+    np.testing.assert_array_equal(r["step"].cpu().numpy(), full["step"].cpu().numpy())
+    np.testing.assert_array_equal(r["t"].cpu().numpy(), full["t"].cpu().numpy())
+    gn2.close()

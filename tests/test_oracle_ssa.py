@@ -97,3 +97,53 @@ def test_resume_is_bit_identical(orc):
     np.testing.assert_array_equal(rest["last"], full["last"])
     np.testing.assert_allclose(rest["t"], full["t"], rtol=1e-12)
     assert np.all(full["X"] >= 0)
+
+
+def test_ssa_until_birth_death_poisson_at_sample_times(orc):
+    """Birth-death from 0 (birth 5, death 0.5 per molecule): X(t) is Poisson
+    with mean 10 (1 - exp(-t / 2)) at every sample time; every realization
+    stops before the time limit with T_END."""
+    from scipy import stats
+    net = W.network_from_lists(1, [(W.RT_SOURCE, (-1, -1), 5.0, [(0, 1)]),
+                                   (W.RT_UNI, (0, -1), 0.5, [(0, -1)])])
+    X0 = np.zeros((6000, 1), dtype=np.int32)
+    ts = np.array([0.0, 1.0, 5.0, 20.0])
+    o = orc.ssa_until(net, X0, t_end=20.0, sample_times=ts, nthreads=8)
+    assert (o["status"] == orc.ST_T_END).all() and (o["t"] <= 20.0).all()
+    assert (o["traj"][:, 0, 0] == 0).all()
+    for k, tk in enumerate(ts[1:], start=1):
+        lam = 10.0 * (1.0 - np.exp(-0.5 * tk))
+        x = o["traj"][:, k, 0]
+        hi = int(x.max()) + 1
+        obs = np.bincount(x, minlength=hi + 1).astype(float)
+        exp = stats.poisson.pmf(np.arange(hi + 1), lam) * x.size
+        exp[-1] += stats.poisson.sf(hi, lam) * x.size
+        keep = exp >= 5
+        obs_m = np.append(obs[keep], obs[~keep].sum())
+        exp_m = np.append(exp[keep], exp[~keep].sum())
+        assert stats.chisquare(obs_m, exp_m * obs_m.sum() / exp_m.sum()).pvalue > 1e-3
+
+
+def test_ssa_until_absorption_holds_state_and_resumes(orc):
+    """Pure decay: after absorption the remaining samples hold 0; a run split
+    at an intermediate time limit equals one run (the time stays at the last
+    reaction, so the waiting time that crossed the limit is redrawn from the
+    same counter and the same time)."""
+    net = W.network_from_lists(1, [(W.RT_UNI, (0, -1), 1.0, [(0, -1)])])
+    X0 = np.full((300, 1), 5, dtype=np.int32)
+    ts = np.linspace(0.0, 50.0, 11)
+    o = orc.ssa_until(net, X0, t_end=50.0, sample_times=ts)
+    assert (o["status"] & orc.ST_ABSORBED).all() and (o["X"] == 0).all()
+    assert (o["traj"][:, -1, 0] == 0).all()
+    assert (np.diff(o["traj"][:, :, 0], axis=1) <= 0).all()      # counts only fall
+    net2 = W.random_network(N=30, M=50, seed=12)
+    X1 = W.initial_counts(30, 20, seed=13)
+    full = orc.ssa_until(net2, X1, t_end=0.05, sample_times=[0.01, 0.03, 0.05])
+    h = orc.ssa_until(net2, X1, t_end=0.02, sample_times=[0.01, 0.03, 0.05])
+    r = orc.ssa_until(net2, h["X"], t_end=0.05, t=h["t"], step=h["step"],
+                      sample_times=[0.01, 0.03, 0.05])
+    np.testing.assert_array_equal(r["X"], full["X"])
+    np.testing.assert_array_equal(r["step"], full["step"])
+    np.testing.assert_array_equal(r["t"], full["t"])
+    np.testing.assert_array_equal(h["traj"][:, 0], full["traj"][:, 0])
+    np.testing.assert_array_equal(r["traj"][:, 1:], full["traj"][:, 1:])
