@@ -73,6 +73,7 @@ struct RInfo {  // chunk partials of one realization
 struct SItem {     // selections [s0, s1) of realization b
   int64_t a0, o0;  // first element / first output index of the realization
   uint32_t M, b, s0, s1;
+  uint32_t p0, nch;  // its chunk partials
 };
 struct Part {                 // a chunk's partial result
   unsigned long long hi, lo;  // FP32 data: exact sum (hi:lo) 2^e; FP64: lo = sum bits
@@ -115,6 +116,8 @@ struct Params {
   int64_t bound_stride;
   uint32_t bound_given;  // caller's bounds: checked like ar_select_k's
   uint32_t zero_status;  // the reduction reports all-zero realizations
+  uint32_t fold;         // the selection takes T from the chunk partials and the
+                         // first range of a realization writes {T, sum}, status
 };
 
 // ===========================================================================
@@ -539,6 +542,75 @@ __global__ void __launch_bounds__(kBNT) k_batched_bound(const Params p) {
   }
 }
 
+// Bound (maximum bit pattern) and validity of one realization from its chunk
+// partials; with `write` also its FP64 total (chunk sums aligned to one bit
+// above the largest exponent -- chunk sums are < 2^108 units, so 2^21 of them
+// fit in 128 bits; bits below 2^-96 of the maximum are dropped -- added
+// exactly and rounded once; FP64 data: FP64 sums in chunk order), stored by
+// lane 0 as {T, sum} ({NaN, NaN} when invalid), and the status bits.
+template <typename TS>
+__device__ __forceinline__ void realization_bound(const Params& p, uint32_t p0, uint32_t nch,
+                                                  uint32_t b, bool write, unsigned long long& vm,
+                                                  uint32_t& bd, uint32_t& st_acc) {
+  const uint32_t lane = threadIdx.x & 31u;
+  vm = 0;
+  bd = 0;
+  int emax = INT32_MIN;
+  if constexpr (sizeof(TS) == 4) {
+    uint32_t v32 = 0;
+    for (uint32_t k = lane; k < nch; k += 32) {
+      const Part& q = p.parts[p0 + k];
+      v32 = max(v32, (uint32_t)q.vmax);
+      bd |= q.bad;
+      emax = max(emax, q.e);
+    }
+    vm = __reduce_max_sync(kFull, v32);
+  } else {
+    for (uint32_t k = lane; k < nch; k += 32) {
+      const Part& q = p.parts[p0 + k];
+      const unsigned long long x = q.vmax;
+      vm = x > vm ? x : vm;
+      bd |= q.bad;
+    }
+    vm = warp_max_u64(vm);
+  }
+  bd = __reduce_or_sync(kFull, bd);
+  if (!write) return;
+  double sum = 0.0;
+  if (!bd) {
+    if constexpr (sizeof(TS) == 4) {
+      emax = __reduce_max_sync(kFull, emax) + 1;
+      U128 acc;
+      for (uint32_t k = lane; k < nch; k += 32) {
+        const Part& q = p.parts[p0 + k];
+        U128 y;
+        y.hi = q.hi;
+        y.lo = q.lo;
+        acc = add128(acc, shr128(y, emax - q.e));
+      }
+      acc = warp_sum128(acc);
+      if (lane == 0) sum = u128_to_double(acc, emax);
+    } else {
+      if (lane == 0)
+        for (uint32_t k = 0; k < nch; ++k)
+          sum = __dadd_rn(sum, __longlong_as_double((long long)p.parts[p0 + k].lo));
+    }
+  }
+  if (lane == 0) {
+    double* o = p.bound_sum + 2 * (size_t)b;
+    if (bd) {
+      st_acc |= (bd & 1u) ? AR_STATUS_BAD_ALPHA : 0u;
+      st_acc |= (bd & 2u) ? AR_STATUS_UNSUPPORTED : 0u;
+      o[0] = o[1] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: no selections
+    } else {
+      o[0] = sizeof(TS) == 4 ? (double)__uint_as_float((uint32_t)vm)
+                             : __longlong_as_double((long long)vm);
+      o[1] = sum;
+      if (p.zero_status && vm == 0) st_acc |= AR_STATUS_ALL_ZERO;
+    }
+  }
+}
+
 // One warp per realization: bound, total and status from its chunk partials.
 template <typename TS>
 __global__ void __launch_bounds__(kBNT) k_batched_combine(const Params p) {
@@ -551,54 +623,9 @@ __global__ void __launch_bounds__(kBNT) k_batched_combine(const Params p) {
       p0 = p.rinfo[b].p0;
       nch = p.rinfo[b].nch;
     }
-    unsigned long long vm = 0;
-    uint32_t bd = 0;
-    int emax = INT32_MIN;
-    for (uint32_t k = lane; k < nch; k += 32) {
-      const Part& q = p.parts[p0 + k];
-      const unsigned long long x = q.vmax;
-      vm = x > vm ? x : vm;
-      bd |= q.bad;
-      emax = max(emax, q.e);
-    }
-    vm = warp_max_u64(vm);
-    bd = __reduce_or_sync(kFull, bd);
-    double sum = 0.0;
-    if (!bd) {
-      if constexpr (sizeof(TS) == 4) {
-        // align every chunk to one bit above the largest exponent (chunk
-        // sums are < 2^108 units, so 2^21 of them fit in 128 bits; bits
-        // below 2^-96 of the maximum are dropped), add exactly, round once
-        emax = __reduce_max_sync(kFull, emax) + 1;
-        U128 acc;
-        for (uint32_t k = lane; k < nch; k += 32) {
-          const Part& q = p.parts[p0 + k];
-          U128 y;
-          y.hi = q.hi;
-          y.lo = q.lo;
-          acc = add128(acc, shr128(y, emax - q.e));
-        }
-        acc = warp_sum128(acc);
-        if (lane == 0) sum = u128_to_double(acc, emax);
-      } else {
-        if (lane == 0)
-          for (uint32_t k = 0; k < nch; ++k)
-            sum = __dadd_rn(sum, __longlong_as_double((long long)p.parts[p0 + k].lo));
-      }
-    }
-    if (lane == 0) {
-      double* o = p.bound_sum + 2 * (size_t)b;
-      if (bd) {
-        st_acc |= (bd & 1u) ? AR_STATUS_BAD_ALPHA : 0u;
-        st_acc |= (bd & 2u) ? AR_STATUS_UNSUPPORTED : 0u;
-        o[0] = o[1] = __longlong_as_double(0x7ff8000000000000ll);  // NaN: no selections
-      } else {
-        o[0] = sizeof(TS) == 4 ? (double)__uint_as_float((uint32_t)vm)
-                               : __longlong_as_double((long long)vm);
-        o[1] = sum;
-        if (p.zero_status && vm == 0) st_acc |= AR_STATUS_ALL_ZERO;
-      }
-    }
+    unsigned long long vm;
+    uint32_t bd;
+    realization_bound<TS>(p, p0, nch, b, true, vm, bd, st_acc);
   }
   st_acc = __reduce_or_sync(kFull, st_acc);
   if (lane == 0 && st_acc) atomicOr(p.status, st_acc);
@@ -712,7 +739,7 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
       if (i >= qe) return false;
     }
     int64_t a0 = 0, o0 = 0;
-    uint32_t M = 0, b = 0, s0 = 0, s1 = 0;
+    uint32_t M = 0, b = 0, s0 = 0, s1 = 0, p0 = 0, nch = 1;
     if (p.sitems) {
       const SItem& si = p.sitems[i];
       a0 = si.a0;
@@ -721,8 +748,11 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
       b = si.b;
       s0 = si.s0;
       s1 = si.s1;
+      p0 = si.p0;
+      nch = si.nch;
     } else {
       b = i;
+      p0 = i;
       int64_t v = 0;
       if (lane < 2) v = __ldg(p.offsets + b + lane);
       else if (lane < 4) v = __ldg(p.out_offsets + b + lane - 2);
@@ -734,9 +764,20 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
       s0 = 0;
       s1 = o1 > o0 ? (uint32_t)(o1 - o0) : 0u;
     }
-    // the bound: from k_batched_combine (NaN: invalid realization, already
-    // reported) or the caller's (NaN, < 0 or infinite: BAD_BOUND)
-    const double T = __ldcg(p.bound_in + (size_t)b * (size_t)p.bound_stride);
+    // the bound: from the chunk partials (the realization's first range also
+    // writes {T, sum} and the status), or the caller's (NaN, < 0 or
+    // infinite: BAD_BOUND); NaN marks an invalid realization, reported once
+    double T;
+    if (p.fold) {
+      unsigned long long vm;
+      uint32_t bd;
+      realization_bound<TS>(p, p0, nch, b, s0 == 0, vm, bd, st_acc);
+      if (bd) T = __longlong_as_double(0x7ff8000000000000ll);
+      else if constexpr (sizeof(TS) == 4) T = (double)__uint_as_float((uint32_t)vm);
+      else T = __longlong_as_double((long long)vm);
+    } else {
+      T = __ldcg(p.bound_in + (size_t)b * (size_t)p.bound_stride);
+    }
     const float Tf = __double2float_rn(T);
     int32_t* out = p.idx + o0;
     uint32_t st = 0;
@@ -932,7 +973,7 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
 
 // The reduction and combine kernels (bound_sum and status).
 template <typename TS>
-int launch_bound(const Params& p, bool stream_path, cudaStream_t s) {
+int launch_bound(const Params& p, bool stream_path, bool combine, cudaStream_t s) {
   const DeviceInfo& d = device_info();
   const uint32_t sms = (uint32_t)(d.sm_count > 0 ? d.sm_count : 1);
   const uint32_t nitems = p.ritems ? p.nr : p.B;
@@ -945,7 +986,7 @@ int launch_bound(const Params& p, bool stream_path, cudaStream_t s) {
     k_batched_bound<TS><<<grid, kBNT, 0, s>>>(p);
   }
   const int rc = check_launch();
-  if (rc) return rc;
+  if (rc || !combine) return rc;
   const uint32_t cgrid = std::max(1u, std::min(sms * 8u, (p.B + kBWarps - 1) / kBWarps));
   k_batched_combine<TS><<<cgrid, kBNT, 0, s>>>(p);
   return check_launch();
@@ -987,6 +1028,7 @@ struct ar_plan {
   unsigned char* d_scratch;  // Scratch | parts[NR]
   std::vector<int64_t> off, oo;  // host copies of the offsets (schedule rebuilds)
   std::vector<double> cost;
+  std::vector<RInfo> rinfo;
 };
 
 namespace {
@@ -1031,6 +1073,8 @@ void build_selection(const ar_plan& pl, uint32_t grid, double gshare, std::vecto
       s.b = (uint32_t)b;
       s.s0 = s0;
       s.s1 = (uint32_t)std::min<uint64_t>(K, (uint64_t)s0 + per);
+      s.p0 = pl.rinfo[b].p0;
+      s.nch = pl.rinfo[b].nch;
       sitems.push_back(s);
       s0 = s.s1;
     } while (s0 < K);
@@ -1147,6 +1191,7 @@ extern "C" int ar_plan_create(const int64_t* h_offsets, const int64_t* h_out_off
     }
   }
   p->nr = (uint32_t)ritems.size();
+  p->rinfo = rinfo;
   const size_t scratch_bytes = sizeof(Scratch) + sizeof(Part) * ritems.size();
   cudaError_t e = cudaMalloc(&p->d_ritems, sizeof(RItem) * ritems.size());
   if (e == cudaSuccess) e = cudaMalloc(&p->d_rinfo, sizeof(RInfo) * rinfo.size());
@@ -1280,8 +1325,8 @@ extern "C" int ar_bound_batched(const void* d_alpha_cat, int dtype, const int64_
   p.bound_sum = d_bound_sum;
   p.zero_status = 1u;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  return dtype == AR_F32 ? launch_bound<float>(p, stream_path, s)
-                         : launch_bound<double>(p, stream_path, s);
+  return dtype == AR_F32 ? launch_bound<float>(p, stream_path, true, s)
+                         : launch_bound<double>(p, stream_path, true, s);
 }
 
 extern "C" int ar_select_batched_bounded(const void* d_alpha_cat, int dtype,
@@ -1331,11 +1376,10 @@ extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64
   if (!d_bound_sum) return AR_ERR_ARG;
   if (!aligned(d_bound_sum, 8)) return AR_ERR_ALIGN;
   p.bound_sum = d_bound_sum;
-  p.bound_in = d_bound_sum;
-  p.bound_stride = 2;
+  p.fold = 1u;  // the selection kernel combines the chunk partials itself
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  rc = dtype == AR_F32 ? launch_bound<float>(p, stream_path, s)
-                       : launch_bound<double>(p, stream_path, s);
+  rc = dtype == AR_F32 ? launch_bound<float>(p, stream_path, false, s)
+                       : launch_bound<double>(p, stream_path, false, s);
   if (rc) return rc;
   return dispatch_select(dtype, cmp, p, sel_grid, shape, s);
 }
