@@ -242,12 +242,12 @@ int ar_select_batched_bounded(const void *d_alpha_cat, int dtype, const int64_t 
  * propensities):
  *   - the reduction chunks: each realization cut into ceil(M_b / 1024)
  *     chunks of equal length (16 bytes each);
- *   - the selection work: ranges of 32 selections.  The costliest
+ *   - the selection work: ranges of 64 selections.  The costliest
  *     realizations (estimated cost K_b (0.6 + ln M_b) + 0.05 M_b) are
  *     assigned to the persistent CTAs of the selection kernel by
  *     longest-processing-time-first list scheduling (each CTA's home list);
  *     the cheapest ones, 30% of the estimated cost by default, form a
- *     global queue that balances the CTAs' finishing times (32 bytes per
+ *     global queue that balances the CTAs' finishing times (40 bytes per
  *     range).  Default tile: 16 warps per CTA, 2 CTAs per SM;
  *     ar_plan_autotune picks tile and share on the caller's data;
  *   - device scratch for the chunk partials (32 bytes per chunk).
