@@ -59,7 +59,7 @@ constexpr uint32_t kChunk = 1024;  // reduction chunk (elements)
 constexpr int kVPL = kChunk / 32;  // elements per lane (register path)
 constexpr uint32_t kSItem = 64;     // selections per home work item
 constexpr uint32_t kGItem = 64;     // selections per global-queue work item
-constexpr int kU = 2;               // Philox blocks per lane per round
+constexpr int kU = 3;               // Philox blocks per lane per round
 
 // ---- plan-built work items -------------------------------------------------
 struct RItem {  // one reduction chunk: alpha_cat[e0, e0 + n)
