@@ -286,6 +286,21 @@ int ar_plan_autotune(ar_plan *plan, const void *d_alpha_cat, int dtype,
                      const int64_t *d_offsets, const int64_t *d_out_offsets, uint64_t seed,
                      int cmp, double *d_bound_sum, int32_t *d_idx, ar_stats *d_stats,
                      uint32_t *d_status, int reps, int32_t *h_choice, void *stream);
+
+/* ---------------------------------------------------------------------
+ * ar_plan_set_tile -- sets the plan's selection tile directly (a choice
+ * ar_plan_autotune made earlier, or one known to suit the caller's launch
+ * pattern): warps_per_cta in {8, 16, 32}, global_share_pm in 0..1000 (the
+ * estimated cost per mille left to the global queue).  Rebuilds the
+ * selection schedule on the host and uploads it (synchronous; not
+ * capturable; no call with this plan may be running).  Results of
+ * ar_select_batched do not depend on the tile.  CUDA graphs captured with
+ * this plan before the change launch the old tile: recapture them (the
+ * same holds after ar_plan_autotune).
+ * Errors: AR_ERR_ARG for a NULL plan or values outside those sets;
+ * AR_ERR_CUDA when the upload fails.
+ * ------------------------------------------------------------------- */
+int ar_plan_set_tile(ar_plan *plan, int warps_per_cta, int global_share_pm);
 int ar_select_batched(const void *d_alpha_cat, int dtype, const int64_t *d_offsets,
                       const int64_t *d_out_offsets, int64_t B, uint64_t seed,
                       uint64_t sel_offset, uint32_t realization_base, int cmp,

@@ -79,6 +79,7 @@ SIGNATURES = {
     "ar_select_batched_bounded": (_int, [_vp, _int, _vp, _vp, _i64, _vp, _i64, _u64, _u64, _u32,
                                          _int, _u64, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "ar_probe_throughput": (_int, [_int, _vp, _u32, _u32, _u32, _vp, _sz, _vp]),
+    "ar_plan_set_tile": (_int, [_vp, _int, _int]),
 }
 
 
@@ -312,6 +313,12 @@ def ar_plan_autotune(plan, alpha_cat, offsets, out_offsets, seed, cmp, bound_sum
         _dev(stats, torch.int64, "stats"), _dev(status, torch.int32, "status"), reps, choice,
         _stream(stream)), "ar_plan_autotune")
     return tuple(int(x) for x in choice)
+
+
+def ar_plan_set_tile(plan, warps_per_cta, global_share_pm):
+    """Sets the plan's selection tile (warps per CTA, global share per mille)."""
+    _check(lib().ar_plan_set_tile(_plan_ptr(plan), warps_per_cta, global_share_pm),
+           "ar_plan_set_tile")
 
 
 def ar_select_paper(D, bound, K, seed, sel_offset, realization, idx, rejections, stream=None):

@@ -1108,11 +1108,15 @@ int set_schedule(ar_plan& pl, int shape, int gshare_pm) {
     if (e == cudaSuccess) pl.sitems_cap = sitems.size();
   }
   if (e == cudaSuccess && scta.size() > pl.scta_cap) {
+    // room for the largest grid of any tile, so that the array is allocated
+    // once and a launch captured with an earlier tile never reads freed memory
+    const size_t cap = std::max(scta.size(), (size_t)std::max(1, dev.sm_count) *
+                                                 (size_t)(kSelThreadsPerSm / (8 * 32)) + 1);
     cudaFree(pl.d_scta);
     pl.d_scta = nullptr;
     pl.scta_cap = 0;
-    e = cudaMalloc(&pl.d_scta, sizeof(uint32_t) * scta.size());
-    if (e == cudaSuccess) pl.scta_cap = scta.size();
+    e = cudaMalloc(&pl.d_scta, sizeof(uint32_t) * cap);
+    if (e == cudaSuccess) pl.scta_cap = cap;
   }
   if (e == cudaSuccess)
     e = cudaMemcpy(pl.d_sitems, sitems.data(), sizeof(SItem) * sitems.size(),
@@ -1382,6 +1386,18 @@ extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64
                        : launch_bound<double>(p, stream_path, false, s);
   if (rc) return rc;
   return dispatch_select(dtype, cmp, p, sel_grid, shape, s);
+}
+
+extern "C" int ar_plan_set_tile(ar_plan* plan, int warps_per_cta, int global_share_pm) {
+  if (!plan || global_share_pm < 0 || global_share_pm > 1000) return AR_ERR_ARG;
+  int shape = -1;
+  for (int k = 0; k < 3; ++k)
+    if (kSelShapes[k] == warps_per_cta) shape = k;
+  if (shape < 0) return AR_ERR_ARG;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != plan->device) return AR_ERR_ARG;
+  return set_schedule(*plan, shape, global_share_pm);
 }
 
 extern "C" int ar_plan_autotune(ar_plan* plan, const void* d_alpha_cat, int dtype,

@@ -340,3 +340,20 @@ def test_plan_autotune(gb, orc):
     _, idx2, stats2, st2 = gb.select_batched(a, off, oo, plan=plan)
     np.testing.assert_array_equal(idx2.cpu().numpy(), oidx)
     np.testing.assert_array_equal(stats2.cpu().numpy().astype(np.uint64), ostats)
+
+
+@pytest.mark.parametrize("warps,share", [(8, 0), (16, 1000), (32, 250)])
+def test_plan_set_tile(gb, orc, warps, share):
+    """Any tile the plan is set to gives the oracle's results; bad tiles are
+    rejected."""
+    bt = W.batched_uneven(B=300, seed=307, K=48)
+    a, off, oo = _t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets)
+    plan = gb.Plan(bt.offsets, bt.out_offsets)
+    gb.ar_plan_set_tile(plan, warps, share)
+    _, oidx, ostats, _ = orc.select_batched(bt, nthreads=8)
+    _, idx, stats, st = gb.select_batched(a, off, oo, plan=plan)
+    np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
+    np.testing.assert_array_equal(stats.cpu().numpy().astype(np.uint64), ostats)
+    for bad in ((12, 0), (16, -1), (16, 1001)):
+        with pytest.raises(gb.GbarError):
+            gb.ar_plan_set_tile(plan, *bad)
