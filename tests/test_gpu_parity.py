@@ -357,3 +357,35 @@ def test_plan_set_tile(gb, orc, warps, share):
     for bad in ((12, 0), (16, -1), (16, 1001)):
         with pytest.raises(gb.GbarError):
             gb.ar_plan_set_tile(plan, *bad)
+
+
+@pytest.mark.parametrize("tile", [(8, 300), (16, 0), (32, 0)])
+def test_batched_two_calls_in_flight(gb, orc, tile):
+    """Two independent batches, each with its own plan, alternating on two
+    streams (the benchmark's headline pattern): both match the oracle after
+    many overlapping calls."""
+    import torch
+    bts = [W.batched_uneven(B=1500, seed=320 + k, K=128) for k in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    bufs = []
+    for bt in bts:
+        plan = gb.Plan(bt.offsets, bt.out_offsets)
+        gb.ar_plan_set_tile(plan, *tile)
+        bufs.append(dict(
+            a=_t(bt.alpha), off=_t(bt.offsets), oo=_t(bt.out_offsets), plan=plan,
+            bs=torch.empty((bt.B, 2), dtype=torch.float64, device="cuda"),
+            idx=torch.empty(int(bt.out_offsets[-1]), dtype=torch.int32, device="cuda"),
+            stats=torch.zeros(3, dtype=torch.int64, device="cuda"),
+            st=torch.zeros(1, dtype=torch.int32, device="cuda")))
+    torch.cuda.synchronize()
+    for i in range(20):  # ten calls per batch; the counters add up
+        b = bufs[i % 2]
+        gb.ar_select_batched(b["a"], b["off"], b["oo"], 1, 0, 0, 0, 1 << 20, b["plan"], b["bs"],
+                             b["idx"], b["stats"], b["st"], None, streams[i % 2])
+    torch.cuda.synchronize()
+    for bt, b in zip(bts, bufs):
+        obs, oidx, ostats, ost = orc.select_batched(bt, nthreads=8)
+        np.testing.assert_array_equal(b["idx"].cpu().numpy(), oidx)
+        np.testing.assert_array_equal(b["bs"].cpu().numpy()[:, 0], obs[:, 0])
+        np.testing.assert_array_equal(b["stats"].cpu().numpy().astype(np.uint64), 10 * ostats)
+        assert int(b["st"].item()) == ost
