@@ -164,9 +164,11 @@ int ar_select_k(const void *d_alpha, int dtype, int64_t M, const double *d_bound
 /* ---------------------------------------------------------------------
  * ar_select_batched -- many realizations with uneven M_b and K_b:
  * ar_bound_batched followed by ar_select_batched_bounded with each
- * realization's own maximum as its bound (three kernels enqueued on the
- * stream; Section "A GPU acceptance-rejection algorithm": K realizations as
- * K blocks; the text's extension to M beyond one block).
+ * realization's own maximum as its bound, in two kernels enqueued on the
+ * stream: the reduction, then the selections, which combine each
+ * realization's chunk results themselves (Section "A GPU
+ * acceptance-rejection algorithm": K realizations as K blocks; the text's
+ * extension to M beyond one block).
  * Realization b owns alpha_cat[offsets[b] .. offsets[b+1]) and writes
  * K_b = out_offsets[b+1] - out_offsets[b] indices at d_idx[out_offsets[b]].
  * Its bound is its own maximum, computed in the kernel; its Philox

@@ -4,7 +4,8 @@
 // "Implementation"; several blocks per realization when M exceeds a block,
 // Discussion).
 //
-// Three launches on the caller's stream:
+// ar_select_batched is two launches on the caller's stream, the reduction
+// and the selections (ar_bound_batched: the reduction and the combine):
 //
 //   k_bound_reg / k_batched_bound   per-chunk partial results: maximum
 //       (exact, on bit patterns), validity and exact sum of chunks of at most
@@ -20,14 +21,16 @@
 //       FP32 and integer rates, so no FP64 operation touches the elements.
 //   k_batched_combine   one warp per realization: T_b = the maximum of its
 //       chunk maxima, the chunk sums aligned and added exactly in 128 bits and
-//       rounded once to FP64, the status.
+//       rounded once to FP64, the status.  In ar_select_batched the selection
+//       kernel does this instead when it claims a range of the realization
+//       (the bound), and for the realization's first range also the sum.
 //   k_batched_select    the selections.  A plan gives each persistent CTA a
 //       home list of its realizations (the costliest ones, by
-//       longest-processing-time-first list scheduling) in ranges of 32
+//       longest-processing-time-first list scheduling) in ranges of 64
 //       selections claimed in order from a shared-memory counter, so the
-//       warps of an SM work on one or two realizations at a time and the
+//       warps of an SM work on a few realizations at a time and the
 //       gathers hit L1; the cheapest realizations form a global queue of
-//       32-selection ranges that the warps drain once their home list is
+//       64-selection ranges that the warps drain once their home list is
 //       empty.  A lane that finishes a selection takes the next one at once,
 //       so no warp waits for the slowest selection of a realization.  Per
 //       round a lane evaluates U Philox blocks (2U trials) of its own
