@@ -5,12 +5,14 @@
 //
 // One warp owns one realization for the whole call.  Its propensities live in
 // the caller's FP64 array a[M] (global, L1-resident) with an FP32 copy in
-// shared memory for the trial gathers.  After reaction j fires, only the
+// shared memory for the trial gathers; its counts X move to shared memory for
+// the call when the network is small enough.  After reaction j fires, only the
 // reactions that depend on a species j changes are recomputed (the
 // dependency graph of Gibson & Bruck, cited in the Introduction), each as one
 // FP64 rounding of c_r times the exact integer count h_r(X).  The bound is the
-// exact maximum of the FP32 copies (a per-lane maximum over a strided subset,
-// rescanned only when an update lowers it).  The total propensity a_0 is kept
+// exact maximum of the FP32 copies (a per-lane maximum over a strided subset:
+// raised elements update it through a shared-memory maximum, and the subset
+// is rescanned only when the element holding its maximum is lowered).  The total propensity a_0 is kept
 // as an exact 128-bit fixed-point integer (no drift over long runs), and the
 // waiting times tau = ln(1/u)/a_0 of 32 consecutive steps are computed
 // together, one step per lane, because GB300 runs FP64 at a small fraction of
@@ -67,6 +69,8 @@ struct SsaParams {
   uint32_t b_base;
   uint32_t k0, k1;
   uint32_t smem_stride;  // bytes of shared memory per warp
+  uint32_t x_off;        // offset of the counts in a warp's shared memory (XS)
+  uint32_t inc_off;      // offset of the per-lane raised maxima
   // run to a time limit, with trajectory samples (ssa_run_until)
   double t_end;
   const double* samp_t;   // [nsamp] ascending sample times
@@ -157,21 +161,32 @@ __device__ __forceinline__ double unfix128(I128 x, int S) {
   return ldexp(v, -S);
 }
 
-template <int CMP, bool TIMED>
+// XS: the counts live in shared memory during the call (read from and
+// written back to X), when the network is small enough.
+template <int CMP, bool TIMED, bool XS>
 __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t b = blockIdx.x * kWarpsS + warp;
   if (b >= p.B) return;
-  // FP32 (or FP64) copies of the propensities for gathers and the bound
-  float* af = reinterpret_cast<float*>(smem + (size_t)warp * p.smem_stride);
+  // FP32 (or FP64) copies of the propensities for gathers and the bound,
+  // then the counts (XS) and the lanes' raised maxima
+  unsigned char* wsm = smem + (size_t)warp * p.smem_stride;
+  float* af = reinterpret_cast<float*>(wsm);
   double* ad = reinterpret_cast<double*>(af);
+  unsigned long long* inc = reinterpret_cast<unsigned long long*>(wsm + p.inc_off);
   uint32_t st = p.status[b];
   if (st & (AR_STATUS_ABSORBED | AR_STATUS_TRIAL_CAP | AR_STATUS_BAD_ALPHA | AR_STATUS_UNSUPPORTED))
     return;
   const int M = p.M;
-  int32_t* X = p.X + (size_t)b * p.N;
+  int32_t* Xg = p.X + (size_t)b * p.N;
+  int32_t* X = Xg;
+  if constexpr (XS) {
+    X = reinterpret_cast<int32_t*>(wsm + p.x_off);
+    for (int q = (int)lane; q < p.N; q += 32) X[q] = Xg[q];
+    __syncwarp();
+  }
   double* a = p.a + (size_t)b * M;
   const uint32_t bid = p.b_base + b;
   unsigned long long step = p.step[b];
@@ -326,41 +341,47 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
       const int d0 = __ldg(p.dep_ptr + j), d1 = __ldg(p.dep_ptr + j + 1);
       I128 dq{0ull, 0ull};
       uint32_t rescan = 0;  // lanes whose strided maximum may have dropped
+      inc[lane] = 0ull;  // the largest raised element of each lane's subset
+      __syncwarp();
       for (int base = d0; base < d1; base += 32) {
         const int qi = base + (int)lane;
-        if (qi < d1) {
-          const int r = __ldg(p.dep + qi);
+        const bool act = qi < d1;
+        const int r = act ? __ldg(p.dep + qi) : 0;
+        // the owner's maximum before this step's updates: a decrease changes
+        // it only when the element held it
+        const uint32_t owner = act ? ((uint32_t)r & 31u) : lane;
+        const uint32_t om = __shfl_sync(kFull, lmax, owner);
+        const unsigned long long om64 = __shfl_sync(kFull, lmax64, owner);
+        if (act) {
           const double vn = propensity(p, r, X);
           const double vo = a[r];
           a[r] = vn;
           dq = add128(dq, add128(fix128(vn, S, &ovf), neg128(fix128(vo, S, &ovf))));
-          const uint32_t owner = (uint32_t)r & 31u;
           if constexpr (CMP == AR_CMP_F32) {
             const float fo = af[r], fn = __double2float_rn(vn);
             af[r] = fn;
-            if (fn < fo) rescan |= 1u << owner;
+            if (fn < fo && __float_as_uint(fo) == om) rescan |= 1u << owner;
+            if (fn > fo) atomicMax(inc + owner, (unsigned long long)__float_as_uint(fn));
           } else {
             const double o = ad[r];
             ad[r] = vn;
-            if (vn < o) rescan |= 1u << owner;
+            if (vn < o && (unsigned long long)__double_as_longlong(o) == om64)
+              rescan |= 1u << owner;
+            if (vn > o) atomicMax(inc + owner, (unsigned long long)__double_as_longlong(vn));
           }
         }
       }
       a0x = add128(a0x, warp_sum128(dq));
       __syncwarp();
-      // lane maxima: rescan the strided subsets that lost an element, and
-      // take the maximum with every raised element otherwise
+      // lane maxima: rescan the strided subsets whose maximum dropped, and
+      // take the maximum with the raised elements otherwise
       rescan = __reduce_or_sync(kFull, rescan);
       if (CMP == AR_CMP_F32) {
         if (rescan & (1u << lane)) {
           lmax = 0;
           for (int r = lane; r < M; r += 32) lmax = max(lmax, __float_as_uint(af[r]));
         } else {
-          // increases: the raised elements are among this round's updates
-          for (int base = d0; base < d1; ++base) {
-            const int r = __ldg(p.dep + base);
-            if (((uint32_t)r & 31u) == lane) lmax = max(lmax, __float_as_uint(af[r]));
-          }
+          lmax = max(lmax, (uint32_t)inc[lane]);
         }
       } else {
         if (rescan & (1u << lane)) {
@@ -368,11 +389,7 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
           for (int r = lane; r < M; r += 32)
             lmax64 = max(lmax64, (unsigned long long)__double_as_longlong(ad[r]));
         } else {
-          for (int base = d0; base < d1; ++base) {
-            const int r = __ldg(p.dep + base);
-            if (((uint32_t)r & 31u) == lane)
-              lmax64 = max(lmax64, (unsigned long long)__double_as_longlong(ad[r]));
-          }
+          lmax64 = max(lmax64, inc[lane]);
         }
       }
       __syncwarp();
@@ -384,6 +401,10 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
   // waiting times of the steps of the last, partial block
   if (!TIMED && blk_fill > 0 && blk_fill <= 32) flush_block(blk_fill);
   if (ovf) st |= AR_STATUS_UNSUPPORTED;
+  if constexpr (XS) {
+    __syncwarp();
+    for (int q = (int)lane; q < p.N; q += 32) Xg[q] = X[q];
+  }
   if (lane == 0) {
     p.t[b] = t;
     p.step[b] = step;
@@ -514,12 +535,23 @@ int ssa_launch(const ssa_net* net, int64_t B, int32_t* d_X, double* d_a, double*
       !aligned(d_status, 4) || !aligned(d_last, 4) || !aligned(d_trials, 8))
     return AR_ERR_ALIGN;
   if ((uint64_t)realization_base + (uint64_t)B > (1ull << 32)) return AR_ERR_ARG;
+  // per warp: the comparison copies, the lanes' raised maxima, the counts
   const size_t es = cmp == AR_CMP_F32 ? 4 : 8;
-  const uint32_t stride = (uint32_t)(((size_t)(net->M + 32) * es + 15) & ~size_t(15));
-  const size_t smem = (size_t)stride * kWarpsS;
+  const size_t inc_off = ((size_t)net->M * es + 15) & ~size_t(15);
+  const size_t x_off = inc_off + 32 * sizeof(unsigned long long);
+  const size_t with_x = x_off + (((size_t)net->N * 4 + 15) & ~size_t(15));
   const DeviceInfo& dev = device_info();
-  if ((int)smem > (dev.max_smem_optin > 0 ? dev.max_smem_optin : 227 * 1024))
-    return AR_ERR_UNSUPPORTED;
+  const size_t limit = dev.max_smem_optin > 0 ? (size_t)dev.max_smem_optin : 227 * 1024;
+  // counts in shared memory when that keeps four CTAs per SM (the
+  // register limit) or does not lower the CTAs per SM at all
+  const size_t sm_total = 228 * 1024, per_cta_reserved = 1024;
+  auto ctas = [&](size_t stride) {
+    return std::min<size_t>(4, sm_total / (stride * kWarpsS + per_cta_reserved));
+  };
+  const bool xs = with_x * kWarpsS <= limit && ctas(with_x) >= ctas(x_off);
+  const uint32_t stride = (uint32_t)(xs ? with_x : x_off);
+  const size_t smem = (size_t)stride * kWarpsS;
+  if (smem > limit) return AR_ERR_UNSUPPORTED;
   p.rtype = net->d_rtype;
   p.reac = net->d_reac;
   p.rate = net->d_rate;
@@ -543,6 +575,8 @@ int ssa_launch(const ssa_net* net, int64_t B, int32_t* d_X, double* d_a, double*
   p.k0 = (uint32_t)(seed & 0xffffffffu);
   p.k1 = (uint32_t)(seed >> 32);
   p.smem_stride = stride;
+  p.inc_off = (uint32_t)inc_off;
+  p.x_off = (uint32_t)x_off;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const unsigned grid = (unsigned)((B + kWarpsS - 1) / kWarpsS);
   auto go = [&](auto kern) {
@@ -550,11 +584,21 @@ int ssa_launch(const ssa_net* net, int64_t B, int32_t* d_X, double* d_a, double*
     kern<<<grid, kNTS, smem, s>>>(p);
   };
   if (cmp == AR_CMP_F32) {
-    if (timed) go(k_ssa<AR_CMP_F32, true>);
-    else go(k_ssa<AR_CMP_F32, false>);
+    if (xs) {
+      if (timed) go(k_ssa<AR_CMP_F32, true, true>);
+      else go(k_ssa<AR_CMP_F32, false, true>);
+    } else {
+      if (timed) go(k_ssa<AR_CMP_F32, true, false>);
+      else go(k_ssa<AR_CMP_F32, false, false>);
+    }
   } else {
-    if (timed) go(k_ssa<AR_CMP_F64, true>);
-    else go(k_ssa<AR_CMP_F64, false>);
+    if (xs) {
+      if (timed) go(k_ssa<AR_CMP_F64, true, true>);
+      else go(k_ssa<AR_CMP_F64, false, true>);
+    } else {
+      if (timed) go(k_ssa<AR_CMP_F64, true, false>);
+      else go(k_ssa<AR_CMP_F64, false, false>);
+    }
   }
   return check_launch();
 }
