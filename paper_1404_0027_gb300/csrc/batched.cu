@@ -41,6 +41,7 @@
 #include <cstddef>
 #include <numeric>
 #include <queue>
+#include <type_traits>
 #include <utility>
 #include <vector>
 
@@ -108,7 +109,9 @@ struct Params {
   int32_t* idx;
   ar_stats* stats;
   uint32_t* status;
-  unsigned long long cap;
+  unsigned long long cap;  // trials per selection, 1 .. 2^32
+  uint32_t capb;           // ceil(cap / 2): Philox blocks per selection
+  uint32_t cap_m1;         // cap - 1
   uint32_t B;
   uint32_t sel_base;
   uint32_t b_base;
@@ -637,23 +640,25 @@ __global__ void __launch_bounds__(kBNT) k_batched_combine(const Params p) {
 // ===========================================================================
 // Selection kernel
 // ===========================================================================
-template <typename TS>
+// The bound in the comparison's precision.
+template <int CMP>
+using BoundT = std::conditional_t<CMP == AR_CMP_F32, float, double>;
+
+template <typename TS, int CMP>
 struct Lane {
   bool act = false;
   uint32_t sel = 0, cnt = 0, M = 0, b = 0;
   const TS* a = nullptr;
   int32_t* out = nullptr;
-  float Tf = 0.f;
-  double T = 0.0;
+  BoundT<CMP> T = 0;
 };
 
-template <typename TS>
+template <typename TS, int CMP>
 struct WItem {  // the warp's current item (identical in every lane)
   uint32_t b = 0, s = 0, s1 = 0, M = 0;
   const TS* a = nullptr;
   int32_t* out = nullptr;
-  float Tf = 0.f;
-  double T = 0.0;
+  BoundT<CMP> T = 0;
 };
 
 // The comparison operand alpha_j: FP32 or FP64 per the comparison precision.
@@ -672,7 +677,7 @@ __device__ __forceinline__ auto load_alpha(const TS* a, uint32_t j) {
 // `nvalid` trials and its candidate.  All gathers are issued before any test.
 template <typename TS, int CMP>
 __device__ __forceinline__ int eval_blocks(const Params& p, uint32_t cnt, uint32_t sel, uint32_t b,
-                                           uint32_t M, const TS* a, float Tf, double T,
+                                           uint32_t M, const TS* a, BoundT<CMP> T,
                                            uint32_t nvalid, uint32_t& jh) {
   uint4 w[kU];
 #pragma unroll
@@ -692,7 +697,7 @@ __device__ __forceinline__ int eval_blocks(const Params& p, uint32_t cnt, uint32
   for (int t = 2 * kU - 1; t >= 0; --t) {
     const uint32_t wu = (t & 1) ? w[t >> 1].w : w[t >> 1].y;
     bool acc;
-    if constexpr (CMP == AR_CMP_F32) acc = accept_f32(wu, Tf, x[t]);
+    if constexpr (CMP == AR_CMP_F32) acc = accept_f32(wu, T, x[t]);
     else acc = accept_f64(wu, T, x[t]);
     if ((uint32_t)t < nvalid && acc) {
       hit = t;
@@ -716,7 +721,7 @@ struct Claimer {
 // get their indices set to M here and are skipped.
 template <typename TS, int CMP>
 __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Claimer& cl,
-                          WItem<TS>& w, uint32_t& st_acc) {
+                          WItem<TS, CMP>& w, uint32_t& st_acc) {
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
     uint32_t i = 0;
@@ -801,8 +806,8 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
     w.M = M;
     w.a = reinterpret_cast<const TS*>(p.alpha) + a0;
     w.out = out;
-    w.Tf = Tf;
-    w.T = T;
+    if constexpr (CMP == AR_CMP_F32) w.T = Tf;
+    else w.T = T;
     return true;
   }
 }
@@ -823,8 +828,8 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
   __syncthreads();
   SelCounters cnt;
   uint32_t st_acc = 0;
-  Lane<TS> L;
-  WItem<TS> cur;
+  Lane<TS, CMP> L;
+  WItem<TS, CMP> cur;
   Claimer cl;
   bool have = next_item<TS, CMP>(p, &s_queue, q_end, cl, cur, st_acc);
   bool tail = false;
@@ -844,7 +849,6 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
           L.b = cur.b;
           L.a = cur.a;
           L.out = cur.out;
-          L.Tf = cur.Tf;
           L.T = cur.T;
         }
         const uint32_t ni = __popc(idle);
@@ -861,19 +865,18 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
       // ---- steady round: U Philox blocks of the lane's own selection
       if (L.act) {
         uint32_t jh = 0;
-        const unsigned long long base = 2ull * L.cnt;
-        const unsigned long long left = p.cap - base;
-        const uint32_t nvalid = left < 2 * kU ? (uint32_t)left : 2u * kU;
-        const int hit =
-            eval_blocks<TS, CMP>(p, L.cnt, L.sel, L.b, L.M, L.a, L.Tf, L.T, nvalid, jh);
+        // trials left: cap - 2 cnt = d + 1 (an active lane has cnt < capb)
+        const uint32_t d = p.cap_m1 - 2u * L.cnt;
+        const uint32_t nvalid = d >= 2u * kU - 1u ? 2u * kU : d + 1u;
+        const int hit = eval_blocks<TS, CMP>(p, L.cnt, L.sel, L.b, L.M, L.a, L.T, nvalid, jh);
         if (hit >= 0) {
           L.out[L.sel] = (int32_t)jh;
-          cnt.trials += base + (unsigned long long)hit + 1ull;
+          cnt.trials += 2ull * L.cnt + (unsigned long long)hit + 1ull;
           cnt.accepted += 1;
           L.act = false;
         } else {
           L.cnt += kU;
-          if (2ull * L.cnt >= p.cap) {
+          if (L.cnt >= p.capb) {
             L.out[L.sel] = (int32_t)L.M;
             cnt.trials += p.cap;
             cnt.capped += 1;
@@ -896,8 +899,7 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
             reinterpret_cast<const TS*>(__shfl_sync(kFull, (unsigned long long)L.a, from));
         int32_t* o2 =
             reinterpret_cast<int32_t*>(__shfl_sync(kFull, (unsigned long long)L.out, from));
-        const float Tf2 = __shfl_sync(kFull, L.Tf, from);
-        const double T2 = __shfl_sync(kFull, L.T, from);
+        const BoundT<CMP> T2 = __shfl_sync(kFull, L.T, from);
         L.act = lane < nA;
         L.sel = sel2;
         L.cnt = cnt2;
@@ -905,7 +907,6 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
         L.b = b2;
         L.a = a2;
         L.out = o2;
-        L.Tf = Tf2;
         L.T = T2;
       }
       // G = 32 >> ceil(log2 nA) lanes per selection, U blocks per lane
@@ -918,17 +919,18 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
       const uint32_t o_cnt = __shfl_sync(kFull, L.cnt, src) + g * kU;
       const uint32_t o_M = __shfl_sync(kFull, L.M, src);
       const uint32_t o_b = __shfl_sync(kFull, L.b, src);
-      const float o_Tf = __shfl_sync(kFull, L.Tf, src);
-      const double o_T = __shfl_sync(kFull, L.T, src);
+      const BoundT<CMP> o_T = __shfl_sync(kFull, L.T, src);
       const TS* o_a =
           reinterpret_cast<const TS*>(__shfl_sync(kFull, (unsigned long long)L.a, src));
       int hit = -1;
       uint32_t jh = 0;
       if (valid) {
-        const unsigned long long base = 2ull * o_cnt;
-        const unsigned long long left = base < p.cap ? p.cap - base : 0ull;
-        const uint32_t nvalid = left < 2 * kU ? (uint32_t)left : 2u * kU;
-        hit = eval_blocks<TS, CMP>(p, o_cnt, o_sel, o_b, o_M, o_a, o_Tf, o_T, nvalid, jh);
+        uint32_t nvalid = 0;
+        if (o_cnt < p.capb) {
+          const uint32_t d = p.cap_m1 - 2u * o_cnt;
+          nvalid = d >= 2u * kU - 1u ? 2u * kU : d + 1u;
+        }
+        hit = eval_blocks<TS, CMP>(p, o_cnt, o_sel, o_b, o_M, o_a, o_T, nvalid, jh);
       }
       const uint32_t bal = __ballot_sync(kFull, hit >= 0);
       const uint32_t seg_lo = (lane << lg) & 31u;
@@ -948,7 +950,7 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
           L.act = false;
         } else {
           L.cnt += (1u << lg) * kU;
-          if (2ull * L.cnt >= p.cap) {
+          if (L.cnt >= p.capb) {
             L.out[L.sel] = (int32_t)L.M;
             cnt.trials += p.cap;
             cnt.capped += 1;
@@ -1297,6 +1299,8 @@ int selection_params(uint64_t seed, uint64_t sel_offset, uint32_t realization_ba
   p.idx = d_idx;
   p.stats = d_stats;
   p.cap = trial_cap;
+  p.capb = (uint32_t)((trial_cap + 1) / 2);
+  p.cap_m1 = (uint32_t)(trial_cap - 1);
   p.sel_base = (uint32_t)sel_offset;
   p.b_base = realization_base;
   p.k0 = (uint32_t)(seed & 0xffffffffu);

@@ -148,14 +148,16 @@ def test_select_degenerate(gb, orc):
 
 
 # -------------------------------------------------------- ar_select_batched
-def _check_batched(gb, orc, bt, cmp=0, seed=1, sel_offset=0, realization_base=0, plan=False):
+def _check_batched(gb, orc, bt, cmp=0, seed=1, sel_offset=0, realization_base=0, plan=False,
+                   trial_cap=1 << 20):
     pl = gb.Plan(bt.offsets, bt.out_offsets) if plan else None
     bs, idx, stats, st = gb.select_batched(_t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets),
                                            seed=seed, sel_offset=sel_offset,
-                                           realization_base=realization_base, cmp=cmp, plan=pl)
+                                           realization_base=realization_base, cmp=cmp,
+                                           trial_cap=trial_cap, plan=pl)
     obs, oidx, ostats, ost = orc.select_batched(bt, seed=seed, sel_offset=sel_offset,
                                                 realization_base=realization_base, cmp=cmp,
-                                                nthreads=8)
+                                                trial_cap=trial_cap, nthreads=8)
     g = idx.cpu().numpy()
     mism = np.flatnonzero(g != oidx)
     assert mism.size == 0, f"{mism.size} mismatches of {g.size}, first at {mism[:5]}"
@@ -389,3 +391,13 @@ def test_batched_two_calls_in_flight(gb, orc, tile):
         np.testing.assert_array_equal(b["bs"].cpu().numpy()[:, 0], obs[:, 0])
         np.testing.assert_array_equal(b["stats"].cpu().numpy().astype(np.uint64), 10 * ostats)
         assert int(b["st"].item()) == ost
+
+
+@pytest.mark.parametrize("plan", [False, True])
+@pytest.mark.parametrize("cap", [1, 2, 3, 5, 6, 7, 13, 64])
+def test_batched_trial_cap(gb, orc, cap, plan):
+    """Small trial caps, odd and even, below, at and above the trials of one
+    round: capped selections get the sentinel M_b and count cap trials, in
+    steady rounds and in the tail where lanes share selections."""
+    bt = W.batched_uneven(B=200, seed=330, m_lo=16, m_hi=3000, K=96)
+    _check_batched(gb, orc, bt, cmp=0, seed=4, plan=plan, trial_cap=cap)
