@@ -401,3 +401,20 @@ def test_batched_trial_cap(gb, orc, cap, plan):
     steady rounds and in the tail where lanes share selections."""
     bt = W.batched_uneven(B=200, seed=330, m_lo=16, m_hi=3000, K=96)
     _check_batched(gb, orc, bt, cmp=0, seed=4, plan=plan, trial_cap=cap)
+
+
+@pytest.mark.parametrize("plan", [False, True])
+@pytest.mark.parametrize("cmp", [0, 1])
+def test_batched_tiny_bounds(gb, orc, cmp, plan):
+    """Realizations whose maximum lies near and below 2^-102 (where the FP32
+    bound can no longer be pre-scaled by 2^-24 exactly) and in the subnormal
+    range: the same indices as the oracle."""
+    rng = np.random.default_rng(331)
+    vecs = []
+    for e in (-100, -102, -103, -110, -126, -140, -149):
+        v = np.ldexp(rng.uniform(0.5, 1.0, size=300), e).astype(np.float32)
+        v[rng.integers(0, 300, size=20)] = 0.0
+        vecs.append(v)
+    vecs.append(W.skewed(500, seed=9).astype(np.float32))
+    _check_batched(gb, orc, W.batch_from_vectors(vecs, [200] * len(vecs)), cmp=cmp, seed=5,
+                   plan=plan)
