@@ -703,6 +703,54 @@ def main():
                   "workload": "one FP64 vector M=1024 alpha~U(0,1], K=1000 selections, "
                               "ar_bound + ar_select_k, FP64 comparison, CUDA graph"}
 
+    # ---- the single-vector workloads: skewed (M = 1029 lognormal with 30 %
+    # zeros, K = 65536) and wide range (M = 2^20 spread over 12 decades,
+    # K = 2^20), one ar_bound + ar_select_k per call, FP32 comparison -------
+    def single_leg(alpha_np, K, reps):
+        d_al = torch.from_numpy(alpha_np).to(dev)
+        bs1 = torch.empty(2, dtype=torch.float64, device=dev)
+        st1 = torch.zeros(1, dtype=torch.int32, device=dev)
+        wk = torch.zeros(max(gb.ar_bound_workspace_size(d_al.numel(), 0), 16),
+                         dtype=torch.uint8, device=dev)  # zero-filled before first use
+        ix = {c: torch.empty(K, dtype=torch.int32, device=dev) for c in (0, 1)}
+        sts = {c: torch.zeros(3, dtype=torch.int64, device=dev) for c in (0, 1)}
+
+        def call(c):
+            gb.ar_bound(d_al, bs1, st1, wk, stream)
+            gb.ar_select_k(d_al, bs1, K, SEED, 0, 0, c, 1 << 20, ix[c], sts[c], st1, stream)
+        with torch.cuda.stream(stream):
+            call(gb.AR_CMP_F64)
+            call(gb.AR_CMP_F32)
+        stream.synchronize()
+        mism = float((ix[0] != ix[1]).float().mean().item())
+        trials = int(sts[0][0].item())
+        g1 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g1, stream=stream):
+            call(gb.AR_CMP_F32)
+        for _ in range(5):
+            g1.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                g1.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        blocks = trials / 2.0
+        return {"value": K / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms,
+                "trials_per_selection": trials / K,
+                "alu": {"achieved": blocks / (ms * 1e-3), "peak": alu_peak,
+                        "unit": "Philox4x32-10 blocks/s", "frac": blocks / (ms * 1e-3) / alu_peak},
+                "fp32_vs_fp64_index_mismatch": mism, "status": int(st1.item())}
+
+    single = {
+        "skewed": dict(single_leg(W.skewed(1029, seed=200), 65536, 400),
+                       workload="M=1029 FP32 lognormal(0,2), 309 zeros (seed 200), K=65536"),
+        "wide_range": dict(single_leg(W.wide_range(1 << 20, seed=400), 1 << 20, 40),
+                           workload="M=2^20 FP32 10^U(-6,6) (seed 400), K=2^20")}
+
     # ---- full batched SSA: 10^4 realizations x 10^4 steps ------------------
     ssa = None
     if not args.no_ssa:
@@ -798,6 +846,7 @@ def main():
            "step_hbm": step_hbm,
            "cpu_baseline": cpu,
            "fp64_plain": fp64_plain,
+           "single_vector": single,
            "ssa": ssa,
            "accuracy": {"fp32_vs_fp64_index_mismatch": mismatch,
                         "fp32_vs_fp64_paired_tv_mean": paired_tv,

@@ -6,7 +6,9 @@
 // precision when that loses nothing the comparison uses) and, when no bound
 // is given, reduces the exact maximum itself from that copy -- the bound
 // reduction fused into the selection kernel.  Warps then run the warp-level
-// selection engine of select.cuh over contiguous ranges of selection ids.
+// selection engine of select.cuh over contiguous ranges of selection ids,
+// with 1, 2 or 4 Philox blocks per lane per round as the expected trials per
+// selection (M T / sum of the staged copy) are few, moderate or many.
 // Vectors larger than the shared-memory budget are gathered from global
 // memory (they stay L2-resident: 2^20 FP32 propensities are 4 MB of a
 // 129 MB L2).
@@ -18,6 +20,7 @@ namespace gbar {
 namespace {
 
 constexpr int kNT = 512;
+
 constexpr int kWarps = kNT / 32;
 constexpr size_t kScratch = (size_t)kWarps * 64 * sizeof(uint32_t);
 
@@ -49,9 +52,11 @@ __global__ void __launch_bounds__(kNT) k_select(const SelParams p) {
   const TS* g_alpha = static_cast<const TS*>(p.alpha);
   __shared__ unsigned long long s_max[kWarps];
   __shared__ unsigned long long s_umax[kWarps];
+  __shared__ float s_sum[kWarps];
 
   // 1. stage alpha (and its maximum when no bound is given)
   unsigned long long smax = 0, umax = 0;  // bit-pattern maxima of the staged values
+  float ssum = 0.f;  // rough total: sets the Philox blocks per lane per round
   if (SMEM) {
     for (uint32_t i = threadIdx.x; i < M; i += kNT) {
       const TS x = __ldg(g_alpha + i);
@@ -59,6 +64,7 @@ __global__ void __launch_bounds__(kNT) k_select(const SelParams p) {
       if constexpr (sizeof(TA) == sizeof(TS)) y = x;
       else y = __double2float_rn(x);
       s_alpha[i] = y;
+      ssum += (float)y;
       if (p.bound == nullptr) {
         if constexpr (sizeof(TA) == 4) {
           const uint32_t bits = __float_as_uint(y);
@@ -102,6 +108,22 @@ __global__ void __launch_bounds__(kNT) k_select(const SelParams p) {
     T = *p.bound;
     __syncthreads();
   }
+  // Philox blocks per lane per round, from the expected trials per selection
+  // M T / sum (staged vectors; 2 otherwise): many blocks per round amortise
+  // the round's ballots when acceptance is rare, few waste little when it is
+  // frequent.  The results do not depend on it.
+  int U = 2;
+  if (SMEM) {
+    ssum = warp_sum_f32(ssum);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = ssum;
+    __syncthreads();
+    float tot = 0.f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) tot += s_sum[w];
+    const float E = (float)M * (float)T / tot;
+    if (E <= 4.f) U = 1;
+    else if (E > 48.f) U = 4;
+  }
 
   // 2. bound checks (identical in every CTA)
   uint32_t st = 0;
@@ -122,6 +144,14 @@ __global__ void __launch_bounds__(kNT) k_select(const SelParams p) {
         atomicOr(p.status, st);
     } else {
       SelCounters c;
+      auto run_select = [&](int u, uint32_t q0, uint32_t q1, const auto& acc, SelCounters& cc) {
+        if (u == 1)
+          warp_select<1>(q0, q1, p.sel_base, M, p.b, p.k0, p.k1, p.cap, acc, p.idx, scr, cc);
+        else if (u == 4)
+          warp_select<4>(q0, q1, p.sel_base, M, p.b, p.k0, p.k1, p.cap, acc, p.idx, scr, cc);
+        else
+          warp_select<2>(q0, q1, p.sel_base, M, p.b, p.k0, p.k1, p.cap, acc, p.idx, scr, cc);
+      };
       if constexpr (CMP == AR_CMP_F32) {
         auto acc = [&](uint32_t j, uint32_t w) -> bool {
           float a;
@@ -130,7 +160,7 @@ __global__ void __launch_bounds__(kNT) k_select(const SelParams p) {
           else a = __double2float_rn(__ldg(g_alpha + j));
           return accept_f32(w, Tf, a);
         };
-        warp_select(q, q_end, p.sel_base, M, p.b, p.k0, p.k1, p.cap, acc, p.idx, scr, c);
+        run_select(U, q, q_end, acc, c);
       } else {
         auto acc = [&](uint32_t j, uint32_t w) -> bool {
           double a;
@@ -138,7 +168,7 @@ __global__ void __launch_bounds__(kNT) k_select(const SelParams p) {
           else a = (double)__ldg(g_alpha + j);
           return accept_f64(w, T, a);
         };
-        warp_select(q, q_end, p.sel_base, M, p.b, p.k0, p.k1, p.cap, acc, p.idx, scr, c);
+        run_select(U, q, q_end, acc, c);
       }
       flush_counters(c, p.stats);
       if (c.capped) {

@@ -5,8 +5,9 @@
 // "active", one per lane in a compact list (lane i holds the selection id and
 // the next Philox counter of the i-th active selection).  Each round gives
 // every active selection G = 32 >> ceil(log2(active)) lanes; lane g of a
-// selection's segment evaluates the Philox block t/2 = cnt + g, i.e. trials
-// 2(cnt+g) and 2(cnt+g)+1.  A ballot over the lanes and a find-first-set in
+// selection's segment evaluates the U Philox blocks t/2 = cnt + g U ..
+// cnt + g U + U - 1, i.e. trials 2(cnt + g U) .. 2(cnt + g U + U) - 1, its
+// lowest accepted one first.  A ballot over the lanes and a find-first-set in
 // each segment pick the lowest accepted trial, so the result is the one the
 // sequential AR loop of the paper (Section "A GPU acceptance-rejection
 // algorithm") produces on the same stream, whatever G is.  Finished
@@ -28,7 +29,7 @@ struct SelCounters {
 
 // acc(j, w) -> bool : the acceptance test of candidate j with uniform word w.
 // idx[i] receives the result of local selection i (global id sel_base + i).
-template <class Acc>
+template <int U, class Acc>
 __device__ __forceinline__ void warp_select(uint32_t q, const uint32_t q_end, const uint32_t sel_base,
                                             const uint32_t M, const uint32_t b, const uint32_t k0,
                                             const uint32_t k1, const unsigned long long cap,
@@ -55,31 +56,46 @@ __device__ __forceinline__ void warp_select(uint32_t q, const uint32_t q_end, co
     const uint32_t g = lane & ((1u << lg) - 1u);
     const bool valid = owner < nA;
     const uint32_t sel = __shfl_sync(kFull, my_sel, owner & 31u);
-    const uint32_t cnt = __shfl_sync(kFull, my_cnt, owner & 31u) + g;
-    const uint4 w = philox10(make_uint4(cnt, sel_base + sel, b, 0u), k0, k1);
+    const uint32_t cnt = __shfl_sync(kFull, my_cnt, owner & 31u) + g * U;
+    uint4 w[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) w[u] = philox10(make_uint4(cnt + u, sel_base + sel, b, 0u), k0, k1);
+    uint32_t j[2 * U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      j[2 * u] = candidate(w[u].x, M);
+      j[2 * u + 1] = candidate(w[u].z, M);
+    }
+    int hit = -1;  // the lowest accepted trial of this lane, 0 .. 2U - 1
+    uint32_t jh = 0;
     const unsigned long long t0 = 2ull * cnt;
-    const uint32_t j0 = candidate(w.x, M);
-    const uint32_t j1 = candidate(w.z, M);
-    const bool a0 = valid && t0 < cap && acc(j0, w.y);
-    const bool a1 = valid && t0 + 1ull < cap && acc(j1, w.w);
-    const uint32_t bal = __ballot_sync(kFull, a0 || a1);
-    const uint32_t code = a0 ? (j0 << 1) : ((j1 << 1) | 1u);
+#pragma unroll
+    for (int t = 2 * U - 1; t >= 0; --t) {
+      const uint32_t wu = (t & 1) ? w[t >> 1].w : w[t >> 1].y;
+      if (valid && t0 + (unsigned long long)t < cap && acc(j[t], wu)) {
+        hit = t;
+        jh = j[t];
+      }
+    }
+    const uint32_t bal = __ballot_sync(kFull, hit >= 0);
     // State lane i reads its segment [i*G, i*G + G) of the ballot.
     const uint32_t seg_lo = (lane << lg) & 31u;
     const uint32_t seg_mask = lg == 5u ? kFull : ((1u << (1u << lg)) - 1u);
     const uint32_t seg = (bal >> seg_lo) & seg_mask;
     const uint32_t src = seg_lo + (uint32_t)(__ffs(seg) - 1);
-    const uint32_t got = __shfl_sync(kFull, code, src & 31u);
+    const uint32_t got_j = __shfl_sync(kFull, jh, src & 31u);
+    const uint32_t got_h = (uint32_t)__shfl_sync(kFull, hit, src & 31u);
     bool done = false;
     if (lane < nA) {
       if (seg) {
-        const uint32_t t_acc = 2u * (my_cnt + (src - seg_lo)) + (got & 1u);
-        idx[my_sel] = (int32_t)(got >> 1);
-        ctr.trials += (unsigned long long)t_acc + 1ull;
+        const unsigned long long t_acc =
+            2ull * (my_cnt + (src - seg_lo) * U) + (unsigned long long)got_h;
+        idx[my_sel] = (int32_t)got_j;
+        ctr.trials += t_acc + 1ull;
         ctr.accepted += 1;
         done = true;
       } else {
-        my_cnt += 1u << lg;
+        my_cnt += (1u << lg) * U;
         if (2ull * my_cnt >= cap) {
           idx[my_sel] = (int32_t)M;
           ctr.trials += cap;
