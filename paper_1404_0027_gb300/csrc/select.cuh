@@ -68,11 +68,14 @@ __device__ __forceinline__ void warp_select(uint32_t q, const uint32_t q_end, co
     }
     int hit = -1;  // the lowest accepted trial of this lane, 0 .. 2U - 1
     uint32_t jh = 0;
+    // trials of this lane below the cap: min(2U, cap - 2 cnt)
     const unsigned long long t0 = 2ull * cnt;
+    const uint32_t nvalid =
+        (!valid || t0 >= cap) ? 0u : (cap - t0 < 2u * U ? (uint32_t)(cap - t0) : 2u * U);
 #pragma unroll
     for (int t = 2 * U - 1; t >= 0; --t) {
       const uint32_t wu = (t & 1) ? w[t >> 1].w : w[t >> 1].y;
-      if (valid && t0 + (unsigned long long)t < cap && acc(j[t], wu)) {
+      if ((uint32_t)t < nvalid && acc(j[t], wu)) {
         hit = t;
         jh = j[t];
       }
