@@ -65,7 +65,6 @@ extern "C" {
 #define AR_STATUS_TRIAL_CAP 4u  /* a selection hit trial_cap; sentinel M   */
 #define AR_STATUS_BAD_BOUND 8u  /* bound NaN, inf, < 0 (or inf in FP32)    */
 #define AR_STATUS_ABSORBED 16u  /* SSA realization reached a0 = 0          */
-#define AR_STATUS_TIMEOUT 32u   /* a bounded device wait gave up           */
 #define AR_STATUS_UNSUPPORTED 64u /* a batched realization with M_b >= 2^31 */
 #define AR_STATUS_T_END 128u      /* SSA realization reached its time limit    */
 
@@ -124,9 +123,13 @@ int ar_bound(const void *d_alpha, int dtype, int64_t M, double *d_bound_sum,
  *   M is limited to AR_BOUND_NOALLOC_MAX_M_F32 (FP32) or
  *   AR_BOUND_NOALLOC_MAX_M_F64 (FP64) elements; larger M returns
  *   AR_ERR_UNSUPPORTED before anything is enqueued.
- *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   Every call looks up the array's device address (cudaGetSymbolAddress,
+ *   which allocates nothing) with the caller's device current, so a device
+ *   reset or another context never leaves a stale address behind.  The
+ *   first call on a device may load the library's device code: make it
  *   before any stream capture.
+ *   All argument checks (ARG, UNSUPPORTED, ALIGN) come before anything is
+ *   enqueued.
  *   All calls share the one array (each clears the part that must start at
  *   zero): calls that overlap on the GPU -- on different streams, or from
  *   different host threads -- race on it and must be serialised.

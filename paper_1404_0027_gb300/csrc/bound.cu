@@ -12,8 +12,6 @@
 // input).  Multi-CTA launches finish in the last CTA to arrive, which
 // combines the per-CTA partials in CTA order (deterministic) and returns the
 // workspace header to zero, so a call is a single kernel launch.
-#include <mutex>
-
 #include "device.cuh"
 #include "host.hpp"
 
@@ -262,9 +260,6 @@ constexpr int kNoAllocMaxCtas = 4096;
 constexpr size_t kNoAllocScratchBytes = sizeof(BoundWork) + (size_t)kNoAllocMaxCtas * 16;
 static_assert((int64_t)kNoAllocMaxCtas * kNT * kEptF32 == AR_BOUND_NOALLOC_MAX_M_F32, "limit");
 static_assert((int64_t)kNoAllocMaxCtas * kNT * kEptF64 == AR_BOUND_NOALLOC_MAX_M_F64, "limit");
-
-std::mutex g_noalloc_mu;
-void* g_noalloc_scratch[64] = {};  // device address of the array, per device ordinal
 }  // namespace
 }  // namespace gbar
 
@@ -272,37 +267,31 @@ static __device__ __align__(256) unsigned char g_bound_noalloc_scratch[gbar::kNo
 
 extern "C" int ar_bound_noalloc(const void* d_alpha, int dtype, int64_t M, double* d_bound_sum,
                                 uint32_t* d_status, void* stream) {
+  // Every check that can reject the call comes before anything is enqueued.
   if (M < 0 || !valid_dtype(dtype) || !d_bound_sum || !d_status || (M > 0 && !d_alpha))
     return AR_ERR_ARG;
   const int64_t limit = dtype == AR_F64 ? AR_BOUND_NOALLOC_MAX_M_F64 : AR_BOUND_NOALLOC_MAX_M_F32;
   if (M > limit) return AR_ERR_UNSUPPORTED;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  if (!aligned(d_alpha, dtype_size(dtype)) || !aligned(d_bound_sum, 8) || !aligned(d_status, 4))
+    return AR_ERR_ALIGN;
+  // The host-side name of the array is only a stand-in for it: ask the
+  // runtime for its device address in the current device's context.  This
+  // is done on every call (it allocates nothing), so the address is never
+  // stale after a device reset or under another context.  The first call
+  // on a device may load the library's device code: make it before any
+  // stream capture.
+  void* scratch = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&scratch, g_bound_noalloc_scratch);
   if (e != cudaSuccess) {
     set_cuda_error(e);
     return AR_ERR_CUDA;
   }
-  if (dev < 0 || dev >= 64) return AR_ERR_UNSUPPORTED;
-  void* scratch = nullptr;
-  {
-    // Set-up, once per device, with that device current: the host-side name
-    // of the array is only a stand-in, so ask the runtime for its address.
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_scratch[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_bound_noalloc_scratch);
-      if (e != cudaSuccess) {
-        set_cuda_error(e);
-        return AR_ERR_CUDA;
-      }
-      g_noalloc_scratch[dev] = p;
-    }
-    scratch = g_noalloc_scratch[dev];
-  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (M > chunk_of(dtype)) {
-    // The shared array keeps the previous call's contents: clear the
-    // counter and status word the multi-CTA combine starts from.
+    // The array keeps what the previous call left in it.  A complete
+    // multi-CTA call returns the counter and status word to zero itself, but
+    // clearing them here makes this call independent of how the previous one
+    // ended (for instance one that overlapped another call, which races).
     e = cudaMemsetAsync(scratch, 0, sizeof(BoundWork), s);
     if (e != cudaSuccess) {
       set_cuda_error(e);

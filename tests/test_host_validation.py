@@ -69,6 +69,32 @@ def test_bound_arguments(L):
     assert L.ar_bound(*args(work=P + 0x1008)) == AR_ERR_ALIGN
 
 
+# ---------------------------------------------------------- ar_bound_noalloc
+LIMIT_F32, LIMIT_F64 = 33554432, 16777216   # AR_BOUND_NOALLOC_MAX_M_F32 / _F64
+
+
+def test_bound_noalloc_arguments(L):
+    """Every rejection comes back before the CUDA runtime is touched: on a
+    machine without a GPU, a call that reached cudaGetSymbolAddress or a
+    launch would return AR_ERR_CUDA instead of these codes."""
+    AR_ERR_UNSUPPORTED = -5
+    args = lambda **k: (vp(k.get("alpha", P)), k.get("dtype", F32), k.get("M", 1 << 22),
+                        vp(k.get("bs", P + 0x100)), vp(k.get("st", P + 0x200)), None)
+    assert L.ar_bound_noalloc(*args(M=-1)) == AR_ERR_ARG
+    assert L.ar_bound_noalloc(*args(dtype=3)) == AR_ERR_ARG
+    assert L.ar_bound_noalloc(*args(st=0)) == AR_ERR_ARG
+    assert L.ar_bound_noalloc(*args(bs=0)) == AR_ERR_ARG
+    assert L.ar_bound_noalloc(*args(alpha=0)) == AR_ERR_ARG
+    # sizes beyond the static scratch array, for each dtype
+    assert L.ar_bound_noalloc(*args(M=LIMIT_F32 + 1)) == AR_ERR_UNSUPPORTED
+    assert L.ar_bound_noalloc(*args(dtype=F64, M=LIMIT_F64 + 1)) == AR_ERR_UNSUPPORTED
+    # alignment is checked before the scratch header is cleared
+    assert L.ar_bound_noalloc(*args(alpha=P + 2)) == AR_ERR_ALIGN
+    assert L.ar_bound_noalloc(*args(dtype=F64, alpha=P + 4)) == AR_ERR_ALIGN
+    assert L.ar_bound_noalloc(*args(bs=P + 0x104)) == AR_ERR_ALIGN
+    assert L.ar_bound_noalloc(*args(st=P + 0x201)) == AR_ERR_ALIGN
+
+
 # --------------------------------------------------- batched entry points
 B = 100
 
