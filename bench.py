@@ -214,36 +214,37 @@ def reduction_bytes(bt) -> int:
     return 4 * int(bt.offsets[-1]) + 8 * (bt.B + 1) + 16 * bt.B
 
 
-def probe_peaks(gb, dev, stream):
+def probe_peaks(dev, stream):
     """Practical ceilings of trial generation on this GPU (Philox4x32-10
     blocks/s): Philox alone, and Philox with both trials' gathers and the
     FP32 test from a 48 MB table (L2-resident) and a 16 KB table (L1).
     Each probe launch is timed with CUDA events on `stream`, median of 5."""
     import torch
+    from paper_1404_0027_gb300 import probe
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     tps, n = 1024, 2048
     out = torch.empty(sms * tps, dtype=torch.int32, device=dev)
     big = torch.rand(12 << 20, dtype=torch.float32, device=dev)
     small = torch.rand(4096, dtype=torch.float32, device=dev)
     res = {}
-    for name, mode, table in (("philox_only", gb.AR_PROBE_PHILOX, None),
-                              ("philox_gather_l2_48MB", gb.AR_PROBE_PHILOX_GATHER, big),
-                              ("philox_gather_l1_16KB", gb.AR_PROBE_PHILOX_GATHER, small)):
+    for name, mode, table in (("philox_only", probe.PHILOX, None),
+                              ("philox_gather_l2_48MB", probe.PHILOX_GATHER, big),
+                              ("philox_gather_l1_16KB", probe.PHILOX_GATHER, small)):
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             for _ in range(2):
-                gb.ar_probe_throughput(mode, table, n, tps, out, stream)
+                probe.throughput(mode, table, n, tps, out, stream)
             ms = []
             for _ in range(5):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                gb.ar_probe_throughput(mode, table, n, tps, out, stream)
+                probe.throughput(mode, table, n, tps, out, stream)
                 e1.record(stream)
                 e1.synchronize()
                 ms.append(e0.elapsed_time(e1))
         res[name] = sms * tps * n / (float(np.median(ms)) * 1e-3)
     res["unit"] = "Philox4x32-10 blocks/s"
-    res["probe"] = f"ar_probe_throughput, {tps} threads/SM x {n} blocks per thread"
+    res["probe"] = f"gbar_probe_throughput, {tps} threads/SM x {n} blocks per thread"
     return res
 
 
@@ -556,7 +557,7 @@ def main():
     reps = min(K, 3000)
     red_ms = time_alone(bound_only, reps)
     sel_ms = time_alone(select_only, reps)
-    probes = probe_peaks(gb, dev, stream)
+    probes = probe_peaks(dev, stream)
 
     # ---- rooflines ---------------------------------------------------------
     peak, peak_kind, peaks = measured_peaks()

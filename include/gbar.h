@@ -431,31 +431,6 @@ int ssa_run_until(const ssa_net *net, int64_t B, int32_t *d_X, double *d_a, doub
                   int32_t nspec, int32_t *d_traj, int32_t *d_last, uint32_t *d_status,
                   uint64_t *d_trials, void *stream);
 
-/* ---------------------------------------------------------------------
- * ar_probe_throughput -- measurement aid, not part of the method: the
- * practical ceilings of trial generation on this GPU.  Launches
- * SM count x threads_per_sm / 256 blocks of 256 threads; every thread
- * evaluates blocks_per_thread Philox4x32-10 blocks with the selection's
- * counter layout (Section "A GPU acceptance-rejection algorithm": two
- * random numbers per trial) and
- *   AR_PROBE_PHILOX          folds their words together;
- *   AR_PROBE_PHILOX_GATHER   also computes both trials' candidates
- *                            j = mulhi(w, M), gathers d_table[j] and applies
- *                            the FP32 acceptance test.
- * The caller times the launch (CUDA events) and divides the Philox blocks,
- * SM count x threads_per_sm x blocks_per_thread, by the time.
- *   d_table          [M] FP32 (mode AR_PROBE_PHILOX_GATHER; 0 < M < 2^31).
- *   blocks_per_thread  even, > 0.
- *   threads_per_sm   a positive multiple of 256.
- *   d_out            [out_words] uint32, one word per launched thread
- *                    (AR_ERR_ARG if smaller).
- * ------------------------------------------------------------------- */
-#define AR_PROBE_PHILOX 0
-#define AR_PROBE_PHILOX_GATHER 1
-int ar_probe_throughput(int mode, const float *d_table, uint32_t M, uint32_t blocks_per_thread,
-                        uint32_t threads_per_sm, uint32_t *d_out, size_t out_words,
-                        void *stream);
-
 #ifdef __cplusplus
 }
 #endif

@@ -37,8 +37,6 @@ AR_F32 = 0
 AR_F64 = 1
 AR_CMP_F32 = 0
 AR_CMP_F64 = 1
-AR_PROBE_PHILOX = 0
-AR_PROBE_PHILOX_GATHER = 1
 
 _lock = threading.Lock()
 _lib = None
@@ -77,7 +75,6 @@ SIGNATURES = {
     "ar_select_it": (_int, [_vp, _int, _i64, _i64, _u64, _u64, _u32, _vp, _vp, _vp, _sz, _vp]),
     "ar_select_batched_bounded": (_int, [_vp, _int, _vp, _vp, _i64, _vp, _i64, _u64, _u64, _u32,
                                          _int, _u64, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
-    "ar_probe_throughput": (_int, [_int, _vp, _u32, _u32, _u32, _vp, _sz, _vp]),
     "ar_plan_set_tile": (_int, [_vp, _int, _int]),
 }
 
@@ -337,15 +334,6 @@ def ar_select_it(alpha, K, seed, sel_offset, realization, idx, status, work, str
         _dev(alpha, name="alpha"), _dtype_code(alpha), alpha.numel(), K, seed, sel_offset,
         realization, _dev(idx, torch.int32, "idx"), _dev(status, torch.int32, "status"),
         _dev(work, name="work"), nbytes, _stream(stream)), "ar_select_it")
-
-
-def ar_probe_throughput(mode, table, blocks_per_thread, threads_per_sm, out, stream=None):
-    """Launches the throughput probe (timed by the caller)."""
-    M = 0 if table is None else table.numel()
-    tp = None if table is None else _dev(table, torch.float32, "table")
-    _check(lib().ar_probe_throughput(mode, tp, M, blocks_per_thread, threads_per_sm,
-                                     _dev(out, torch.int32, "out"), out.numel(), _stream(stream)),
-           "ar_probe_throughput")
 
 
 def select_paper(D, K, T, seed=1, sel_offset=0, realization=0, stream=None):

@@ -1,7 +1,8 @@
-"""Builds libgbar.so (the C-ABI library) from csrc/*.cu for sm_103a.
+"""Builds libgbar.so (the C-ABI library) from csrc/*.cu for sm_103a, and the
+benchmark's probe library probe/libgbar_probe.so from probe/*.cu.
 
 Each translation unit is compiled in parallel with nvcc, then linked into a
-shared library next to this file.  No cmake; a rebuild happens only when a
+shared library next to its sources.  No cmake; a rebuild happens only when a
 source or header is newer than the library.
 """
 from __future__ import annotations
@@ -18,6 +19,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbar.so")
+PROBE = os.path.join(HERE, "probe")
+PROBE_LIB = os.path.join(PROBE, "libgbar_probe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -35,21 +38,26 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+def probe_sources():
+    return sorted(glob.glob(os.path.join(PROBE, "*.cu")))
+
+
 def _deps():
-    return (sources() + glob.glob(os.path.join(CSRC, "*.cuh")) +
+    return (sources() + probe_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) +
             glob.glob(os.path.join(CSRC, "*.hpp")) + glob.glob(os.path.join(INCLUDE, "*.h")) +
             [os.path.abspath(__file__)])
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(PROBE_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB))
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
 def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+    tag = "probe_" if os.path.dirname(os.path.abspath(src)) == PROBE else ""
+    obj = os.path.join(BUILD, tag + os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -59,21 +67,27 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
+def _link(objs, out: str):
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link of {os.path.basename(out)} failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, out)
+
+
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    """Compile every csrc/*.cu and link libgbar.so; returns its path."""
+    """Compile every csrc/*.cu into libgbar.so and probe/*.cu into
+    probe/libgbar_probe.so; returns the path of libgbar.so."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
-    srcs = sources()
-    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    srcs, psrcs = sources(), probe_sources()
+    with cf.ThreadPoolExecutor(max_workers=min(len(srcs) + len(psrcs), os.cpu_count() or 4)) as ex:
+        objs = list(ex.map(lambda s: _compile(s, extra), srcs + psrcs))
+    _link(objs[:len(srcs)], LIB)
+    _link(objs[len(srcs):], PROBE_LIB)
     return LIB
 
 

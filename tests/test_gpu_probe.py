@@ -1,6 +1,7 @@
-"""GPU: the throughput probe computes what it claims (Philox words of the
-selection's counter layout; candidates, gathers and the FP32 acceptance test),
-checked against the oracle's Philox on every launched thread."""
+"""GPU: the benchmark's throughput probe (libgbar_probe.so, outside the
+product ABI) computes what it claims (Philox words of the selection's counter
+layout; candidates, gathers and the FP32 acceptance test), checked against
+the oracle's Philox on every launched thread."""
 import numpy as np
 import pytest
 
@@ -8,14 +9,14 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def gb():
+def pr():
     import torch
     from paper_1404_0027_gb300 import build
     build.build()
-    from paper_1404_0027_gb300 import binding
-    binding.lib()
+    from paper_1404_0027_gb300 import probe
+    probe.lib()
     assert torch.cuda.is_available()
-    return binding
+    return probe
 
 
 def _words(orc, n, nthreads):
@@ -29,12 +30,12 @@ def _words(orc, n, nthreads):
     return w.reshape(nthreads, n, 4)
 
 
-def test_probe_philox_words(gb, orc):
+def test_probe_philox_words(pr, orc):
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     nthreads = sms * 256
     out = torch.zeros(nthreads, dtype=torch.int32, device="cuda")
-    gb.ar_probe_throughput(gb.AR_PROBE_PHILOX, None, 4, 256, out)
+    pr.throughput(pr.PHILOX, None, 4, 256, out)
     torch.cuda.synchronize()
     w = _words(orc, 4, nthreads)
     want = np.bitwise_xor.reduce(w.reshape(nthreads, -1), axis=1)
@@ -42,14 +43,14 @@ def test_probe_philox_words(gb, orc):
 
 
 @pytest.mark.parametrize("M", [1000, 4096])
-def test_probe_gather_accepts(gb, orc, M):
+def test_probe_gather_accepts(pr, orc, M):
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     nthreads = sms * 256
     rng = np.random.default_rng(M)
     table = rng.random(M, dtype=np.float32)
     out = torch.zeros(nthreads, dtype=torch.int32, device="cuda")
-    gb.ar_probe_throughput(gb.AR_PROBE_PHILOX_GATHER, torch.from_numpy(table).cuda(), 4, 256, out)
+    pr.throughput(pr.PHILOX_GATHER, torch.from_numpy(table).cuda(), 4, 256, out)
     torch.cuda.synchronize()
     w = _words(orc, 4, nthreads).astype(np.uint64)
     acc = np.zeros(nthreads, dtype=np.int64)
@@ -60,12 +61,12 @@ def test_probe_gather_accepts(gb, orc, M):
     np.testing.assert_array_equal(out.cpu().numpy().astype(np.int64), acc)
 
 
-def test_probe_rejects_bad_arguments(gb):
+def test_probe_rejects_bad_arguments(pr):
     import torch
     out = torch.zeros(16, dtype=torch.int32, device="cuda")
-    with pytest.raises(gb.GbarError):
-        gb.ar_probe_throughput(gb.AR_PROBE_PHILOX, None, 3, 256, out)   # odd block count
-    with pytest.raises(gb.GbarError):
-        gb.ar_probe_throughput(gb.AR_PROBE_PHILOX, None, 4, 256, out)   # output too small
-    with pytest.raises(gb.GbarError):
-        gb.ar_probe_throughput(gb.AR_PROBE_PHILOX_GATHER, None, 4, 256, out)  # no table
+    with pytest.raises(RuntimeError):
+        pr.throughput(pr.PHILOX, None, 3, 256, out)   # odd block count
+    with pytest.raises(RuntimeError):
+        pr.throughput(pr.PHILOX, None, 4, 256, out)   # output too small
+    with pytest.raises(RuntimeError):
+        pr.throughput(pr.PHILOX_GATHER, None, 4, 256, out)  # no table
