@@ -36,6 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+from paper_1404_0027_gb300 import accuracy as A  # noqa: E402
 from paper_1404_0027_gb300 import workloads as W  # noqa: E402
 
 # kernels one ar_select_batched call with a plan enqueues (reduction, then
@@ -47,6 +48,7 @@ UNIT = "selections/s"
 B_REAL, K_B, M_LO, M_HI = 4096, 256, 64, 16384
 N_SLOTS = 6                      # 6 x ~52 MB > 129 MB L2
 SEED = 1
+ACC_SAMPLES = 10_000_000         # selections per accuracy comparison (FP32 vs FP64)
 PHILOX_IMAD_PER_BLOCK = 40       # 10 rounds x 2 multiplies x (hi + lo)
 IMAD_PER_SM_CLK = 64             # 32-bit integer multiply-add issue rate per SM per clock
 
@@ -382,22 +384,30 @@ def main():
     stream.synchronize()
     bt0 = slots[0]["bt"]
     g_idx = slots[0]["idx"].cpu().numpy()
-    # FP32 vs FP64 comparison on identical streams (paired mismatch >= paired TV)
-    idx64 = torch.empty_like(slots[0]["idx"])
-    with torch.cuda.stream(stream):
-        launch(slots[0], cmp=gb.AR_CMP_F64, idx=idx64)
-    stream.synchronize()
-    i32 = g_idx
-    i64 = idx64.cpu().numpy()
-    mismatch = float(np.mean(i32 != i64))
-    tvs = []
-    for b in range(0, B_REAL, 64):
-        lo, hi = bt0.out_offsets[b], bt0.out_offsets[b + 1]
-        Mb = int(bt0.offsets[b + 1] - bt0.offsets[b])
-        h32 = np.bincount(i32[lo:hi], minlength=Mb + 1)
-        h64 = np.bincount(i64[lo:hi], minlength=Mb + 1)
-        tvs.append(0.5 * np.abs(h32 - h64).sum() / (hi - lo))
-    paired_tv = float(np.mean(tvs))
+    # FP32 vs FP64 comparison on identical streams (paired mismatch >= paired
+    # TV), over N_ACC_CALLS calls with disjoint selection ids (>= 10^7
+    # selections); cell of a result = (realization b, index j), the sentinel
+    # M_b included
+    n_acc = ACC_SAMPLES // (B_REAL * K_B) + 1
+    b_of = np.repeat(np.arange(B_REAL, dtype=np.int64), np.diff(bt0.out_offsets))
+    cell0 = (bt0.offsets[:-1] + np.arange(B_REAL))[b_of]
+    ncells = int(bt0.offsets[-1]) + B_REAL
+    keys = {gb.AR_CMP_F32: [], gb.AR_CMP_F64: []}
+    acc_idx = torch.empty_like(slots[0]["idx"])
+    for c in range(n_acc):
+        for cmp in keys:
+            with torch.cuda.stream(stream):
+                gb.ar_select_batched(slots[0]["alpha"], slots[0]["off"], slots[0]["oo"], SEED,
+                                     c * K_B, b_base, cmp, 1 << 20, slots[0]["plan"],
+                                     slots[0]["bs"], acc_idx, slots[0]["stats"], slots[0]["st"],
+                                     slots[0]["work"], stream)
+            stream.synchronize()
+            keys[cmp].append(cell0 + acc_idx.cpu().numpy())
+    acc_batched = dict(A.paired(np.concatenate(keys[gb.AR_CMP_F32]),
+                                np.concatenate(keys[gb.AR_CMP_F64]), ncells),
+                       sample=f"{n_acc} ar_select_batched calls on one batch, selection ids "
+                              f"c*{K_B} .. c*{K_B}+{K_B - 1}, FP32 and FP64 comparison")
+    del keys
 
     # ---- CUDA graphs, one per slot (recaptured whenever a plan's tile
     # changes: the launch shape is part of the graph) ----------------------
@@ -451,6 +461,10 @@ def main():
         each slot has its own plan, so two calls may overlap); per-step
         events only on one stream.  -> (ms, per-step ms, accepted, trials,
         status)"""
+        # the warm-up replays run on the pipe streams: let every one of them
+        # finish before the counters are cleared on torch's current stream,
+        # so that no warm-up CTA adds to the timed region's counts
+        torch.cuda.synchronize()
         for s in slots:
             s["stats"].zero_()
             s["st"].zero_()
@@ -487,7 +501,7 @@ def main():
     t_wall0 = time.time()
     # one call at a time (per-step latency), with the autotuned tiles
     replay(graphs, 1, args.warmup)
-    ms1, kern_ms, _, _, st1 = timed_run(graphs, 1, nvtx=True)
+    ms1, kern_ms, acc1, trials1, st1 = timed_run(graphs, 1, nvtx=True)
     # two batches in flight: smaller CTAs share SMs with the other call's
     # kernels better, so the tile is picked again for this launch pattern
     pipe_tiles = []
@@ -514,11 +528,18 @@ def main():
         gb.ar_plan_set_tile(s["plan"], *t[:2])
     time.sleep(0.2)
     sampler.stop()
+    # every step selects B x K_b indices; the counters of the timed region
+    # must say exactly that (no selection hits the trial cap on this data)
+    sel_per_step = B_REAL * K_B
+    for name, acc in (("one call at a time", acc1), ("two in flight", accepted)):
+        if acc != K * sel_per_step:
+            raise RuntimeError(f"{name}: {acc} accepted selections counted in the timed "
+                               f"region, expected {K} steps x {sel_per_step}")
     ms1 = reduce_max(ms1, dist, dev)
     elapsed_ms = reduce_max(elapsed_ms, dist, dev)
-    accepted_all = int(reduce_sum(accepted, dist, dev))
-    value = accepted_all / (elapsed_ms * 1e-3)
-    value_one_stream = accepted_all / (ms1 * 1e-3)
+    sel_all = world * K * sel_per_step
+    value = sel_all / (elapsed_ms * 1e-3)
+    value_one_stream = sel_all / (ms1 * 1e-3)
 
     # ---- per-kernel durations: the two steps of the call, each replayed
     # alone from its own graphs (CUDA events on the launching stream) -----
@@ -564,21 +585,41 @@ def main():
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     clk = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = IMAD_PER_SM_CLK * sm_count * clk * 1e6 / PHILOX_IMAD_PER_BLOCK
-    blocks_per_launch = trials / K / 2.0
+    blocks_per_launch = trials / K / 2.0      # the timed region's own trials
     sel_s = float(sel_ms.mean()) * 1e-3
     red_s = float(red_ms.mean()) * 1e-3
-    # the dominant kernel: the selections, bound by 32-bit integer multiply
-    # issue (Philox); work = the Philox blocks the accepted trials need
-    roofline = {"bound": "alu", "achieved": blocks_per_launch / sel_s, "peak": alu_peak,
-                "unit": "Philox4x32-10 blocks/s", "frac": blocks_per_launch / sel_s / alu_peak,
-                "traffic": profiled_traffic("k_batched_select_batched_uneven.md"),
-                "kernel": "k_batched_select<float, AR_CMP_F32> (ar_select_batched_bounded)",
-                "peak_from": f"{IMAD_PER_SM_CLK} IMAD/clk/SM x {sm_count} SMs x {clk:.0f} MHz / "
-                             f"{PHILOX_IMAD_PER_BLOCK} IMAD per block",
-                "work_per_launch": blocks_per_launch, "trials_per_launch": trials / K,
-                "kernel_ms_mean": sel_s * 1e3, "kernel_ms_median": float(np.median(sel_ms)),
-                "microbench": probes,
-                "frac_of_microbench_philox": blocks_per_launch / sel_s / probes["philox_only"]}
+    alg_bytes = float(np.mean([algorithmic_bytes(s["bt"]) for s in slots]))
+    call_s = elapsed_ms / K * 1e-3               # per batch, two calls in flight
+    step_s = float(kern_ms.mean()) * 1e-3        # per call, one call at a time
+    # the headline: the whole call against the HBM roofline (algorithmic
+    # bytes: alpha and the offsets read once, indices and {T, sum} written)
+    roofline = {"bound": "hbm", "achieved": alg_bytes / call_s / 1e9, "peak": peak,
+                "unit": "GB/s", "frac": alg_bytes / call_s / 1e9 / peak,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)" if peak_kind == "measured"
+                else peak_kind,
+                "traffic": profiled_traffic("ar_select_batched_call_batched_uneven.md"),
+                "kernel": "ar_select_batched: k_bound_reg + k_batched_select<float, AR_CMP_F32> "
+                          "(two kernels per call), two independent calls in flight",
+                "algorithmic_bytes_per_launch": alg_bytes, "us_per_call": call_s * 1e6,
+                "one_call_at_a_time": {"achieved": alg_bytes / step_s / 1e9,
+                                       "frac": alg_bytes / step_s / 1e9 / peak,
+                                       "us_per_call": step_s * 1e6},
+                "share_reduction": red_s / (red_s + sel_s),
+                "share_selection": sel_s / (red_s + sel_s)}
+    # the selection kernel alone: bound by 32-bit integer multiply issue
+    # (Philox) with random gathers; work = the Philox blocks the accepted
+    # trials consume
+    roofline_alu = {"bound": "alu", "achieved": blocks_per_launch / sel_s, "peak": alu_peak,
+                    "unit": "Philox4x32-10 blocks/s",
+                    "frac": blocks_per_launch / sel_s / alu_peak,
+                    "traffic": profiled_traffic("k_batched_select_batched_uneven.md"),
+                    "kernel": "k_batched_select<float, AR_CMP_F32> (ar_select_batched_bounded)",
+                    "peak_from": f"{IMAD_PER_SM_CLK} IMAD/clk/SM x {sm_count} SMs x "
+                                 f"{clk:.0f} MHz / {PHILOX_IMAD_PER_BLOCK} IMAD per block",
+                    "work_per_launch": blocks_per_launch, "trials_per_launch": trials / K,
+                    "kernel_ms_mean": sel_s * 1e3, "kernel_ms_median": float(np.median(sel_ms)),
+                    "microbench": probes,
+                    "frac_of_microbench_philox": blocks_per_launch / sel_s / probes["philox_only"]}
     red_bytes = float(np.mean([reduction_bytes(s["bt"]) for s in slots]))
     roofline_reduction = {
         "bound": "hbm", "achieved": red_bytes / red_s / 1e9, "peak": peak, "unit": "GB/s",
@@ -588,21 +629,12 @@ def main():
                   "the combine is folded into the selection kernel)",
         "algorithmic_bytes_per_launch": red_bytes, "kernel_ms_mean": red_s * 1e3,
         "kernel_ms_median": float(np.median(red_ms))}
-    alg_bytes = float(np.mean([algorithmic_bytes(s["bt"]) for s in slots]))
-    step_s = float(kern_ms.mean()) * 1e-3
     # inside ar_select_batched the reduction runs without the combine kernel:
     # its share of the step is the step less the selection timed alone
     in_step_s = step_s - sel_s
     if in_step_s > 0:
         roofline_reduction["in_step_ms_derived"] = in_step_s * 1e3
         roofline_reduction["in_step_frac_derived"] = red_bytes / in_step_s / 1e9 / peak
-    step_hbm = {"bound": "hbm", "achieved": alg_bytes / step_s / 1e9, "peak": peak,
-                "unit": "GB/s", "frac": alg_bytes / step_s / 1e9 / peak, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_step": alg_bytes, "step_ms_mean": step_s * 1e3,
-                "note": "one call at a time; with two batches in flight the job moves "
-                        f"{alg_bytes / (elapsed_ms / K * 1e-3) / 1e9:.0f} GB/s "
-                        f"({alg_bytes / (elapsed_ms / K * 1e-3) / 1e9 / peak:.3f} of peak)",
-                "share_reduction": red_s / (red_s + sel_s), "share_selection": sel_s / (red_s + sel_s)}
 
     # ---- end to end through the C ABI with host buffers ------------------
     # Every step copies its inputs from pinned host memory, runs the call and
@@ -713,21 +745,29 @@ def main():
         st1 = torch.zeros(1, dtype=torch.int32, device=dev)
         wk = torch.zeros(max(gb.ar_bound_workspace_size(d_al.numel(), 0), 16),
                          dtype=torch.uint8, device=dev)  # zero-filled before first use
-        ix = {c: torch.empty(K, dtype=torch.int32, device=dev) for c in (0, 1)}
-        sts = {c: torch.zeros(3, dtype=torch.int64, device=dev) for c in (0, 1)}
+        ix = torch.empty(K, dtype=torch.int32, device=dev)
+        sts = torch.zeros(3, dtype=torch.int64, device=dev)
 
-        def call(c):
+        def call(c, k, out, stats):
             gb.ar_bound(d_al, bs1, st1, wk, stream)
-            gb.ar_select_k(d_al, bs1, K, SEED, 0, 0, c, 1 << 20, ix[c], sts[c], st1, stream)
+            gb.ar_select_k(d_al, bs1, k, SEED, 0, 0, c, 1 << 20, out, stats, st1, stream)
+        # accuracy: ACC_SAMPLES selections in one call per comparison precision
+        big = {c: torch.empty(ACC_SAMPLES, dtype=torch.int32, device=dev) for c in (0, 1)}
         with torch.cuda.stream(stream):
-            call(gb.AR_CMP_F64)
-            call(gb.AR_CMP_F32)
+            call(gb.AR_CMP_F64, ACC_SAMPLES, big[1], None)
+            call(gb.AR_CMP_F32, ACC_SAMPLES, big[0], None)
         stream.synchronize()
-        mism = float((ix[0] != ix[1]).float().mean().item())
-        trials = int(sts[0][0].item())
+        i32, i64 = big[0].cpu().numpy(), big[1].cpu().numpy()
+        del big
+        accuracy = dict(A.paired(i32, i64, alpha_np.size + 1),
+                        fp32_law=A.law(i32, alpha_np), fp64_law=A.law(i64, alpha_np))
+        with torch.cuda.stream(stream):
+            call(gb.AR_CMP_F32, K, ix, sts)
+        stream.synchronize()
+        trials = int(sts[0].item())
         g1 = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g1, stream=stream):
-            call(gb.AR_CMP_F32)
+            call(gb.AR_CMP_F32, K, ix, None)
         for _ in range(5):
             g1.replay()
         torch.cuda.synchronize()
@@ -744,7 +784,7 @@ def main():
                 "trials_per_selection": trials / K,
                 "alu": {"achieved": blocks / (ms * 1e-3), "peak": alu_peak,
                         "unit": "Philox4x32-10 blocks/s", "frac": blocks / (ms * 1e-3) / alu_peak},
-                "fp32_vs_fp64_index_mismatch": mism, "status": int(st1.item())}
+                "accuracy": accuracy, "status": int(st1.item())}
 
     single = {
         "skewed": dict(single_leg(W.skewed(1029, seed=200), 65536, 400),
@@ -843,14 +883,17 @@ def main():
                                  "(3 streams, 2 buffer sets)"},
            "gpu_launches": K * LAUNCHES_PER_CALL,
            "roofline": roofline,
+           "roofline_alu": roofline_alu,
            "roofline_reduction": roofline_reduction,
-           "step_hbm": step_hbm,
            "cpu_baseline": cpu,
            "fp64_plain": fp64_plain,
            "single_vector": single,
            "ssa": ssa,
-           "accuracy": {"fp32_vs_fp64_index_mismatch": mismatch,
-                        "fp32_vs_fp64_paired_tv_mean": paired_tv,
+           "accuracy": {"batched_fp32_vs_fp64": acc_batched,
+                        "skewed_fp32_vs_fp64": single["skewed"]["accuracy"],
+                        "wide_range_fp32_vs_fp64": single["wide_range"]["accuracy"],
+                        "note": "FP64 indices of the library are bit-exact with the FP64 oracle "
+                                "(parity tests), so the paired figures are against the oracle",
                         "status": status, "accepted_per_step": accepted / K},
            "kernel_source_hash": kernel_source_hash()}
     print(json.dumps(out), flush=True)
