@@ -67,6 +67,8 @@ def lib():
         L.orc_select_batched_bounded.restype = u32
         L.orc_select_it.argtypes = [vp, i32, i64, i64, u64, u64, u32, vp, i32]
         L.orc_select_it.restype = u32
+        L.orc_it_prefix.argtypes = [vp, i32, i64, vp]
+        L.orc_it_prefix.restype = u32
         L.orc_select_paper.argtypes = [vp, i64, ctypes.c_float, i64, u64, u64, u32, vp, vp, i32]
         L.orc_select_paper.restype = u32
         L.orc_ssa.argtypes = [ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp, vp, vp, i64,
@@ -168,6 +170,16 @@ def select_it(alpha, K, seed=1, sel_offset=0, realization=0, nthreads=1):
     st = lib().orc_select_it(_ptr(a), _dtype_code(a), a.size, K, ctypes.c_uint64(seed),
                              ctypes.c_uint64(sel_offset), realization, _ptr(idx), nthreads)
     return idx, int(st)
+
+
+def it_prefix(alpha):
+    """Running sums of the inverse transform: S_j = the exact sum of
+    alpha_0..alpha_j (each term rounded down to 2^-96 of the maximum's
+    binade), rounded once to FP64 -> (S float64[M], status)."""
+    a = np.ascontiguousarray(alpha)
+    S = np.zeros(a.size, dtype=np.float64)
+    st = lib().orc_it_prefix(_ptr(a), _dtype_code(a), a.size, _ptr(S))
+    return S, int(st)
 
 
 def select_paper(D, K, T=None, seed=1, sel_offset=0, realization=0, nthreads=1):

@@ -24,6 +24,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -292,13 +293,108 @@ static double u53(uint32_t w0, uint32_t w1)
     return (double)m * 0x1p-53;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Running sums of the inverse transform.  Reading: S_j is the exact sum    */
+/* alpha_0 + ... + alpha_j rounded once to the nearest double (ties to     */
+/* even), which is what the method's "running sum" denotes in exact        */
+/* arithmetic; it does not depend on the order the terms are added in.     */
+/* Each propensity enters as a whole number of units U, rounded down:      */
+/*   FP32 data: U = 2^(E - 223), E = max(biased exponent of the max, 1);   */
+/*   FP64 data: U = 2^(E - 1119), E = max(biased exponent of the max, 97). */
+/* The maximum is then below 2^97 units (exact: its 24- or 53-bit          */
+/* significand shifted by 73 or 44 places), so a term loses less than     */
+/* 2^-96 of the maximum, M < 2^31 terms fit in 128 bits, and every nonzero */
+/* S_j = RN(P_j U) is a normal double.                                     */
+/* ------------------------------------------------------------------------ */
+typedef unsigned __int128 orc_u128;
+
+/* value = m 2^q (m the significand as an integer, q its exponent) */
+static void split_value(const void *alpha, int dtype, int64_t j, uint64_t *m, int *q)
+{
+    if (dtype == 0) {
+        uint32_t bits;
+        memcpy(&bits, (const float *)alpha + j, 4);
+        int e = (int)((bits >> 23) & 0xffu);
+        uint64_t f = bits & 0x7fffffu;
+        *m = e ? (f | 0x800000u) : f;
+        *q = (e ? e : 1) - 150;
+    } else {
+        uint64_t bits;
+        memcpy(&bits, (const double *)alpha + j, 8);
+        int e = (int)((bits >> 52) & 0x7ffu);
+        uint64_t f = bits & 0xfffffffffffffull;
+        *m = e ? (f | 0x10000000000000ull) : f;
+        *q = (e ? e : 1) - 1075;
+    }
+}
+
+/* m 2^q in units of 2^uexp, rounded down */
+static orc_u128 to_units(uint64_t m, int q, int uexp)
+{
+    int sh = q - uexp;
+    if (sh >= 0) return (orc_u128)m << sh;
+    if (sh <= -64) return 0;
+    return (orc_u128)(m >> (-sh));
+}
+
+/* n 2^e rounded to the nearest double, ties to even */
+static double u128_scaled(orc_u128 n, int e)
+{
+    if (n == 0) return 0.0;
+    int nb = 0;
+    for (orc_u128 t = n; t; t >>= 1) nb++;
+    if (nb <= 53) return ldexp((double)(uint64_t)n, e);
+    int drop = nb - 53;
+    orc_u128 q = n >> drop;
+    orc_u128 rem = n - (q << drop);
+    orc_u128 half = (orc_u128)1 << (drop - 1);
+    if (rem > half || (rem == half && (q & 1))) q += 1;  /* q <= 2^53: exact in a double */
+    return ldexp((double)(uint64_t)q, e + drop);
+}
+
+/* S[0..M) as above; returns the status bits of orc_bound.  With BAD_ALPHA
+ * set the sums are not defined and S is left untouched. */
+uint32_t orc_it_prefix(const void *alpha, int dtype, int64_t M, double *S)
+{
+    double bs[2];
+    uint32_t status = orc_bound(alpha, dtype, M, bs);
+    if (status & ST_BAD_ALPHA) return status;
+    uint64_t m;
+    int q;
+    int E;
+    if (dtype == 0) {
+        float mx = (float)bs[0];
+        uint32_t bits;
+        memcpy(&bits, &mx, 4);
+        E = (int)((bits >> 23) & 0xffu);
+        if (E < 1) E = 1;
+    } else {
+        uint64_t bits;
+        memcpy(&bits, &bs[0], 8);
+        E = (int)((bits >> 52) & 0x7ffu);
+        if (E < 97) E = 97;
+    }
+    int uexp = dtype == 0 ? E - 223 : E - 1119;
+    orc_u128 P = 0;
+    for (int64_t j = 0; j < M; j++) {
+        split_value(alpha, dtype, j, &m, &q);
+        P += to_units(m, q, uexp);
+        S[j] = u128_scaled(P, uexp);
+    }
+    return status;
+}
+
+/* Selection: the smallest j with S_j > u * a0, a0 = S_{M-1} (one FP64
+ * multiply); if rounding leaves none, the last index with a nonzero
+ * propensity.  All-zero input (a0 = 0) and invalid propensities
+ * (BAD_ALPHA) give the sentinel M. */
 uint32_t orc_select_it(const void *alpha, int dtype, int64_t M, int64_t K,
                        uint64_t seed, uint64_t sel_offset, uint32_t realization,
                        int32_t *idx, int nthreads)
 {
-    double bs[2];
-    uint32_t status = orc_bound(alpha, dtype, M, bs);
-    double a0 = bs[1];
+    double *S = (double *)malloc(sizeof(double) * (size_t)(M > 0 ? M : 1));
+    uint32_t status = orc_it_prefix(alpha, dtype, M, S);
+    double a0 = (M > 0 && !(status & ST_BAD_ALPHA)) ? S[M - 1] : 0.0;
     int64_t last_nz = -1;
     for (int64_t j = 0; j < M; j++)
         if (alpha_at(alpha, dtype, j) > 0.0) last_nz = j;
@@ -315,17 +411,16 @@ uint32_t orc_select_it(const void *alpha, int dtype, int64_t M, int64_t K,
         uint32_t w[4];
         orc_philox4x32_10(ctr, seed, w);
         double target = u53(w[0], w[1]) * a0;
-        double c = 0.0;
         int64_t pick = last_nz;
         for (int64_t j = 0; j < M; j++) {
-            c += alpha_at(alpha, dtype, j);
-            if (c > target) {
+            if (S[j] > target) {
                 pick = j;
                 break;
             }
         }
         idx[i] = (int32_t)pick;
     }
+    free(S);
     return status;
 }
 

@@ -213,6 +213,52 @@ def test_inverse_transform(orc):
     assert np.all(orc.select_it(np.zeros(5), 3)[0] == 5)
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_it_prefix_is_fsum_of_each_prefix(orc, dtype):
+    """Running sums of the inverse transform: the exact prefix sums rounded
+    once (math.fsum returns the correctly rounded sum of its arguments), for
+    data whose terms all lie within 2^73 (FP32) / 2^44 (FP64) of the
+    maximum's binade, so that no term is rounded down to the unit."""
+    rng = np.random.default_rng(5)
+    a = rng.lognormal(0.0, 2.0, 1500).astype(dtype)
+    a[rng.permutation(a.size)[:300]] = 0.0
+    S, st = orc.it_prefix(a)
+    assert st == 0
+    want = [math.fsum(a[:j + 1].astype(np.float64)) for j in range(a.size)]
+    np.testing.assert_array_equal(S, want)
+    # a larger vector on sampled prefixes; index-order FP64 sums differ
+    a = rng.lognormal(0.0, 3.0, 1 << 16).astype(dtype)
+    S, _ = orc.it_prefix(a)
+    for j in rng.integers(0, a.size, 40):
+        assert S[j] == math.fsum(a[:j + 1].astype(np.float64))
+    assert np.any(S != np.cumsum(a.astype(np.float64)))
+
+
+def test_it_prefix_truncation_bound(orc):
+    """Terms far below the maximum enter rounded down to the unit
+    2^(E - 223) (FP32): the sums stay within j units (plus the final
+    rounding) of the exact ones."""
+    a = np.float32([3e20, 1e-10, 7.5, 2e-30, 4.0e10, 1e-25] * 50)
+    S, st = orc.it_prefix(a)
+    assert st == 0
+    E = int(np.float32(3e20).view(np.uint32) >> 23)
+    unit = 2.0 ** (E - 223)
+    for j in range(a.size):
+        exact = math.fsum(a[:j + 1].astype(np.float64))
+        assert abs(S[j] - exact) <= (j + 1) * unit + 2.0 ** -53 * exact
+    # the tiny terms (below one unit) do not move the sum
+    assert S[1] == S[0] and S[3] == S[2]
+
+
+def test_it_invalid_and_zero(orc):
+    for a in (np.float32([1.0, np.nan, 2.0]), np.array([1.0, -1.0, 3.0]),
+              np.float32([np.inf, 1.0])):
+        idx, st = orc.select_it(a, 20)
+        assert st & 1 and np.all(idx == a.size)        # reading: BAD_ALPHA -> sentinel
+    idx, st = orc.select_it(np.zeros(4), 5)
+    assert st == 2 and np.all(idx == 4)
+
+
 def test_batched_oracle_matches_single(orc):
     bt = W.batched_uneven(B=6, seed=3, m_lo=4, m_hi=300, K=40)
     bs, idx, stats, st = orc.select_batched(bt, seed=2, sel_offset=7, realization_base=10)
