@@ -337,16 +337,25 @@ int ar_select_paper(const float *d_D, int64_t M, const double *d_bound, int64_t 
  * ar_select_it -- the direct method's inverse transform, the comparator
  * the paper argues against (Section "The Stochastic Simulation
  * Algorithm": j is the smallest index with alpha_0 + ... + alpha_j >
- * u alpha_0).  The running sums are the sequential FP64 sums in index
- * order (computed once per call by one thread, into the workspace);
- * u = (w0 2^21 + floor(w1 / 2^11)) 2^-53 from counter (0, s, realization,
- * 2); if rounding leaves no running sum above the target, the last
- * non-zero index is taken; alpha_0 <= 0 (or NaN) gives the sentinel M.
- *   d_alpha      [M] FP32/FP64 (dtype).
+ * u alpha_0).  The running sums S_j are the exact prefix sums rounded once
+ * to FP64 (ties to even), so they do not depend on the order of the
+ * additions: each propensity enters as a whole number of units U, rounded
+ * down (FP32 data: U = 2^(E-223); FP64 data: U = 2^(E-1119); E the biased
+ * exponent of the maximum, at least 1 resp. 97 -- a term loses less than
+ * 2^-96 of the maximum), the units are summed exactly in 128-bit integers
+ * by a parallel scan over tiles of 4096 propensities, and every S_j is
+ * rounded once.  u = (w0 2^21 + floor(w1 / 2^11)) 2^-53 from counter
+ * (0, s, realization, 2); the selection is the first S_j > fl(u S_{M-1})
+ * (bisection); if rounding leaves none, the last index with a positive
+ * propensity.  Invalid propensities (BAD_ALPHA) or S_{M-1} = 0 (ALL_ZERO,
+ * including M = 0) give the sentinel M for every selection.  Five kernels
+ * and one memset of the workspace header.
+ *   d_alpha      [M] FP32/FP64 (dtype), M < 2^31.
  *   d_idx        [K] int32 out.
- *   d_status     OR-ed with BAD_ALPHA and ALL_ZERO (as ar_bound).
- *   d_work       ar_select_it_workspace_size(M) bytes, 16-byte aligned,
- *                rewritten by every call.  Calls sharing it must not overlap.
+ *   d_status     OR-ed with BAD_ALPHA and ALL_ZERO.
+ *   d_work       ar_select_it_workspace_size(M) bytes (48 + 8 M rounded up
+ *                to 16, + 16 per tile), 16-byte aligned, rewritten by every
+ *                call.  Calls sharing it must not overlap.
  * ------------------------------------------------------------------- */
 size_t ar_select_it_workspace_size(int64_t M);
 int ar_select_it(const void *d_alpha, int dtype, int64_t M, int64_t K, uint64_t seed,

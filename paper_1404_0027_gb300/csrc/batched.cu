@@ -61,9 +61,18 @@ constexpr int kBNT = kBWarps * 32;
 constexpr int kBCtasPerSm = 2;
 constexpr uint32_t kChunk = 1024;  // reduction chunk (elements)
 constexpr int kVPL = kChunk / 32;  // elements per lane (register path)
-constexpr uint32_t kSItem = 64;     // selections per home work item
-constexpr uint32_t kGItem = 64;     // selections per global-queue work item
-constexpr int kU = 3;               // Philox blocks per lane per round
+#ifndef GBAR_RED_PREFETCH
+#define GBAR_RED_PREFETCH 0
+#endif
+#ifndef GBAR_SEL_ITEM
+#define GBAR_SEL_ITEM 64
+#endif
+#ifndef GBAR_SEL_U
+#define GBAR_SEL_U 3
+#endif
+constexpr uint32_t kSItem = GBAR_SEL_ITEM;  // selections per home work item
+constexpr uint32_t kGItem = GBAR_SEL_ITEM;  // selections per global-queue work item
+constexpr int kU = GBAR_SEL_U;              // Philox blocks per lane per round
 
 // ---- plan-built work items -------------------------------------------------
 struct RItem {  // one reduction chunk: alpha_cat[e0, e0 + n)
@@ -115,7 +124,7 @@ struct Params {
   uint32_t B;
   uint32_t sel_base;
   uint32_t b_base;
-  uint32_t k0, k1;
+  PhiloxKeys keys;  // round keys of the seed
   uint32_t vec_ok;  // alpha_cat is 16-byte aligned (vector loads)
   // selection bounds: T_b = bound_in[b * bound_stride]
   const double* bound_in;
@@ -125,76 +134,6 @@ struct Params {
   uint32_t fold;         // the selection takes T from the chunk partials and the
                          // first range of a realization writes {T, sum}, status
 };
-
-// ===========================================================================
-// Exact integer sums
-// ===========================================================================
-struct U128 {
-  unsigned long long hi = 0, lo = 0;
-};
-__device__ __forceinline__ U128 add128(U128 x, U128 y) {
-  U128 r;
-  r.lo = x.lo + y.lo;
-  r.hi = x.hi + y.hi + (r.lo < x.lo ? 1ull : 0ull);
-  return r;
-}
-__device__ __forceinline__ U128 shl128(unsigned long long x, int s) {  // 0 <= s < 64
-  U128 r;
-  r.lo = x << s;
-  r.hi = s == 0 ? 0ull : (x >> (64 - s));
-  return r;
-}
-__device__ __forceinline__ U128 shr128(U128 x, int s) {  // s >= 0
-  U128 r;
-  if (s >= 128) return r;
-  if (s >= 64) {
-    r.lo = x.hi >> (s - 64);
-    return r;
-  }
-  if (s == 0) return x;
-  r.lo = (x.lo >> s) | (x.hi << (64 - s));
-  r.hi = x.hi >> s;
-  return r;
-}
-__device__ __forceinline__ U128 warp_sum128(U128 x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    U128 y;
-    y.hi = __shfl_xor_sync(kFull, x.hi, o);
-    y.lo = __shfl_xor_sync(kFull, x.lo, o);
-    x = add128(x, y);
-  }
-  return x;
-}
-
-// x * 2^e rounded to the nearest double (ties to even), integer arithmetic
-// only.  The result is a normal double for every FP32 input here.
-__device__ double u128_to_double(U128 x, int e) {
-  if (x.hi == 0 && x.lo == 0) return 0.0;
-  const int nbits = x.hi ? 128 - __clzll((long long)x.hi) : 64 - __clzll((long long)x.lo);
-  int ex = e + nbits - 1;  // exponent of the leading bit
-  unsigned long long mant;
-  if (nbits <= 53) {
-    mant = x.lo << (53 - nbits);
-  } else {
-    const int sh = nbits - 53;  // bits below the kept 53 (1..75)
-    mant = shr128(x, sh).lo;
-    const int hb = sh - 1;      // the half bit
-    const bool half = hb >= 64 ? ((x.hi >> (hb - 64)) & 1ull) : ((x.lo >> hb) & 1ull);
-    const bool sticky = hb >= 64 ? (x.lo != 0 || (x.hi & ((1ull << (hb - 64)) - 1ull)) != 0)
-                                 : (x.lo & ((1ull << hb) - 1ull)) != 0;
-    if (half && (sticky || (mant & 1ull))) {
-      ++mant;
-      if (mant == (1ull << 53)) {
-        mant >>= 1;
-        ++ex;
-      }
-    }
-  }
-  const unsigned long long bits =
-      ((unsigned long long)(ex + 1023) << 52) | (mant & 0xfffffffffffffull);
-  return __longlong_as_double((long long)bits);
-}
 
 // Exact fixed-point windows of non-negative FP32 values, e_ref the biased
 // exponent of their maximum (at least 1); value = m 2^(e - 150), d = e_ref - e:
@@ -470,6 +409,21 @@ __global__ void __launch_bounds__(kBNT, kBCtasPerSm) k_bound_reg(const Params p)
   const uint32_t* u = reinterpret_cast<const uint32_t*>(p.alpha);
   if (it >= p.nr) return;
   const uint32_t lane = threadIdx.x & 31u;
+#if GBAR_RED_PREFETCH
+  // Ask for every chunk of this warp at once (bulk prefetches into L2, no
+  // registers held, nothing waits for them): HBM streams the whole batch at
+  // full rate while the warps reduce, their own loads then hit L2.  Each
+  // prefetch covers a chunk's 16-byte groups only (aligned, inside alpha).
+  for (uint32_t q = it + lane * stride; q < p.nr; q += 32u * stride) {
+    const RItem d = p.ritems[q];
+    const int64_t g0 = (d.e0 + 3) & ~int64_t(3), g1 = (d.e0 + d.n) & ~int64_t(3);
+    if (g1 > g0) {
+      const uint32_t nbytes = (uint32_t)((g1 - g0) * 4);
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(u + g0), "r"(nbytes)
+                   : "memory");
+    }
+  }
+#endif
   auto load = [&](const RItem& d, uint32_t (&v)[kVPL], uint32_t& xs) -> int {
     int64_t g0 = (d.e0 + 3) & ~int64_t(3), g1 = (d.e0 + d.n) & ~int64_t(3);
     if (g1 < g0) g0 = g1 = d.e0;
@@ -673,16 +627,17 @@ __device__ __forceinline__ auto load_alpha(const TS* a, uint32_t j) {
 }
 
 // Evaluates Philox blocks cnt .. cnt + kU - 1 of selection (sel, b): returns
-// the lowest accepted trial offset (0 .. 2kU - 1, or -1) among the first
-// `nvalid` trials and its candidate.  All gathers are issued before any test.
+// the lowest accepted trial offset (0 .. 2kU - 1, or -1) and its candidate.
+// All gathers are issued before any test.  The trial cap is applied by the
+// caller (capped_hit): if the lowest accepted trial lies past the cap, no
+// trial below the cap was accepted.
 template <typename TS, int CMP>
 __device__ __forceinline__ int eval_blocks(const Params& p, uint32_t cnt, uint32_t sel, uint32_t b,
-                                           uint32_t M, const TS* a, BoundT<CMP> T,
-                                           uint32_t nvalid, uint32_t& jh) {
+                                           uint32_t M, const TS* a, BoundT<CMP> T, uint32_t& jh) {
   uint4 w[kU];
 #pragma unroll
   for (int u = 0; u < kU; ++u)
-    w[u] = philox10(make_uint4(cnt + u, p.sel_base + sel, p.b_base + b, 0u), p.k0, p.k1);
+    w[u] = philox10k(make_uint4(cnt + u, p.sel_base + sel, p.b_base + b, 0u), p.keys);
   uint32_t j[2 * kU];
 #pragma unroll
   for (int u = 0; u < kU; ++u) {
@@ -699,12 +654,18 @@ __device__ __forceinline__ int eval_blocks(const Params& p, uint32_t cnt, uint32
     bool acc;
     if constexpr (CMP == AR_CMP_F32) acc = accept_f32(wu, T, x[t]);
     else acc = accept_f64(wu, T, x[t]);
-    if ((uint32_t)t < nvalid && acc) {
+    if (acc) {
       hit = t;
       jh = j[t];
     }
   }
   return hit;
+}
+
+// The lowest accepted trial 2 cnt + hit counts only below the trial cap
+// (cap - 1 - 2 cnt >= 0 for an active selection, whose cnt < ceil(cap / 2)).
+__device__ __forceinline__ int capped_hit(const Params& p, uint32_t cnt, int hit) {
+  return (hit >= 0 && (uint32_t)hit > p.cap_m1 - 2u * cnt) ? -1 : hit;
 }
 
 // Work claiming of one warp: the CTA's home list through a shared-memory
@@ -774,25 +735,42 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
     }
     // the bound: from the chunk partials (the realization's first range also
     // writes {T, sum} and the status), or the caller's (NaN, < 0 or
-    // infinite: BAD_BOUND); NaN marks an invalid realization, reported once
-    double T;
+    // infinite: BAD_BOUND); st = 1 marks an invalid realization, reported
+    // once.  The chunk maxima are bit patterns of non-negative values, so
+    // their checks need no FP64 operation (GB300's FP64 pipe is narrow).
+    BoundT<CMP> Tc = 0;
+    uint32_t st = 0;
     if (p.fold) {
       unsigned long long vm;
       uint32_t bd;
       realization_bound<TS>(p, p0, nch, b, s0 == 0, vm, bd, st_acc);
-      if (bd) T = __longlong_as_double(0x7ff8000000000000ll);
-      else if constexpr (sizeof(TS) == 4) T = (double)__uint_as_float((uint32_t)vm);
-      else T = __longlong_as_double((long long)vm);
+      if (bd) {
+        st = 1;
+      } else if (vm == 0 || M == 0) {
+        st = AR_STATUS_ALL_ZERO;  // the paper's rejection case
+      } else if constexpr (sizeof(TS) == 4) {
+        Tc = (BoundT<CMP>)__uint_as_float((uint32_t)vm);
+      } else {
+        const double T = __longlong_as_double((long long)vm);
+        if constexpr (CMP == AR_CMP_F32) {
+          const float Tf = __double2float_rn(T);
+          if (isinf(Tf)) st = AR_STATUS_BAD_BOUND;
+          Tc = Tf;
+        } else {
+          Tc = T;
+        }
+      }
     } else {
-      T = __ldcg(p.bound_in + (size_t)b * (size_t)p.bound_stride);
+      const double T = __ldcg(p.bound_in + (size_t)b * (size_t)p.bound_stride);
+      const float Tf = __double2float_rn(T);
+      if (p.bound_given && (!(T >= 0.0) || isinf(T))) st = AR_STATUS_BAD_BOUND;
+      else if (T != T) st = 1;
+      else if (CMP == AR_CMP_F32 && isinf(Tf)) st = AR_STATUS_BAD_BOUND;
+      else if (T == 0.0 || M == 0) st = AR_STATUS_ALL_ZERO;  // the paper's rejection case
+      if constexpr (CMP == AR_CMP_F32) Tc = Tf;
+      else Tc = T;
     }
-    const float Tf = __double2float_rn(T);
     int32_t* out = p.idx + o0;
-    uint32_t st = 0;
-    if (p.bound_given && (!(T >= 0.0) || isinf(T))) st = AR_STATUS_BAD_BOUND;
-    else if (T != T) st = 1;
-    else if (CMP == AR_CMP_F32 && isinf(Tf)) st = AR_STATUS_BAD_BOUND;
-    else if (T == 0.0 || M == 0) st = AR_STATUS_ALL_ZERO;  // the paper's rejection case
     if (st) {
       // BAD_BOUND is reported for every realization it hits, ALL_ZERO only
       // for realizations with selections
@@ -806,8 +784,7 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
     w.M = M;
     w.a = reinterpret_cast<const TS*>(p.alpha) + a0;
     w.out = out;
-    if constexpr (CMP == AR_CMP_F32) w.T = Tf;
-    else w.T = T;
+    w.T = Tc;
     return true;
   }
 }
@@ -865,10 +842,8 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
       // ---- steady round: U Philox blocks of the lane's own selection
       if (L.act) {
         uint32_t jh = 0;
-        // trials left: cap - 2 cnt = d + 1 (an active lane has cnt < capb)
-        const uint32_t d = p.cap_m1 - 2u * L.cnt;
-        const uint32_t nvalid = d >= 2u * kU - 1u ? 2u * kU : d + 1u;
-        const int hit = eval_blocks<TS, CMP>(p, L.cnt, L.sel, L.b, L.M, L.a, L.T, nvalid, jh);
+        const int hit =
+            capped_hit(p, L.cnt, eval_blocks<TS, CMP>(p, L.cnt, L.sel, L.b, L.M, L.a, L.T, jh));
         if (hit >= 0) {
           L.out[L.sel] = (int32_t)jh;
           cnt.trials += 2ull * L.cnt + (unsigned long long)hit + 1ull;
@@ -924,14 +899,8 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
           reinterpret_cast<const TS*>(__shfl_sync(kFull, (unsigned long long)L.a, src));
       int hit = -1;
       uint32_t jh = 0;
-      if (valid) {
-        uint32_t nvalid = 0;
-        if (o_cnt < p.capb) {
-          const uint32_t d = p.cap_m1 - 2u * o_cnt;
-          nvalid = d >= 2u * kU - 1u ? 2u * kU : d + 1u;
-        }
-        hit = eval_blocks<TS, CMP>(p, o_cnt, o_sel, o_b, o_M, o_a, o_T, nvalid, jh);
-      }
+      if (valid && o_cnt < p.capb)
+        hit = capped_hit(p, o_cnt, eval_blocks<TS, CMP>(p, o_cnt, o_sel, o_b, o_M, o_a, o_T, jh));
       const uint32_t bal = __ballot_sync(kFull, hit >= 0);
       const uint32_t seg_lo = (lane << lg) & 31u;
       const uint32_t seg_mask = lg == 5u ? kFull : ((1u << (1u << lg)) - 1u);
@@ -1303,8 +1272,7 @@ int selection_params(uint64_t seed, uint64_t sel_offset, uint32_t realization_ba
   p.cap_m1 = (uint32_t)(trial_cap - 1);
   p.sel_base = (uint32_t)sel_offset;
   p.b_base = realization_base;
-  p.k0 = (uint32_t)(seed & 0xffffffffu);
-  p.k1 = (uint32_t)(seed >> 32);
+  p.keys = philox_keys(seed);
   return AR_OK;
 }
 

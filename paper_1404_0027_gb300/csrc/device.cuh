@@ -34,6 +34,36 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
   return c;
 }
 
+// The ten round keys of a Philox4x32-10 key (k0, k1): (k0 + r 0x9E3779B9,
+// k1 + r 0xBB67AE85), r = 0..9, computed once on the host and passed in a
+// kernel's parameters, so that every round XORs a constant operand instead of
+// advancing the key in registers.  philox10k computes what philox10 does.
+struct PhiloxKeys {
+  uint32_t k[20];  // k[2r] = k0 of round r, k[2r + 1] = k1 of round r
+};
+inline PhiloxKeys philox_keys(uint64_t seed) {
+  PhiloxKeys K;
+  uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    K.k[2 * r] = k0;
+    K.k[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return K;
+}
+__device__ __forceinline__ uint4 philox10k(uint4 c, const PhiloxKeys& K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo_a = 0xD2511F53u * c.x;
+    const uint32_t hi_a = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo_b = 0xCD9E8D57u * c.z;
+    const uint32_t hi_b = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi_b ^ c.y ^ K.k[2 * r], lo_b, hi_a ^ c.w ^ K.k[2 * r + 1], lo_a);
+  }
+  return c;
+}
+
 // Candidate index of a trial: floor(w * M / 2^32) (uniform over 0..M-1 up to
 // a 2^-32 preimage lattice).  Requires M < 2^31.
 __device__ __forceinline__ uint32_t candidate(uint32_t w, uint32_t M) {
@@ -91,6 +121,78 @@ __device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, o));
   return v;
+}
+
+// ---------------------------------------------------------------------------
+// Exact integer sums: 128-bit unsigned accumulators and their rounding to FP64.
+// ---------------------------------------------------------------------------
+struct U128 {
+  unsigned long long hi = 0, lo = 0;
+};
+__device__ __forceinline__ U128 add128(U128 x, U128 y) {
+  U128 r;
+  r.lo = x.lo + y.lo;
+  r.hi = x.hi + y.hi + (r.lo < x.lo ? 1ull : 0ull);
+  return r;
+}
+__device__ __forceinline__ U128 shl128(unsigned long long x, int s) {  // 0 <= s < 64
+  U128 r;
+  r.lo = x << s;
+  r.hi = s == 0 ? 0ull : (x >> (64 - s));
+  return r;
+}
+__device__ __forceinline__ U128 shr128(U128 x, int s) {  // s >= 0
+  U128 r;
+  if (s >= 128) return r;
+  if (s >= 64) {
+    r.lo = x.hi >> (s - 64);
+    return r;
+  }
+  if (s == 0) return x;
+  r.lo = (x.lo >> s) | (x.hi << (64 - s));
+  r.hi = x.hi >> s;
+  return r;
+}
+__device__ __forceinline__ U128 warp_sum128(U128 x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    U128 y;
+    y.hi = __shfl_xor_sync(kFull, x.hi, o);
+    y.lo = __shfl_xor_sync(kFull, x.lo, o);
+    x = add128(x, y);
+  }
+  return x;
+}
+
+// x * 2^e rounded to the nearest double (ties to even), integer arithmetic
+// only.  Callers keep every nonzero result at or above the smallest normal
+// double; a result beyond the largest finite double is +inf.
+__device__ inline double u128_to_double(U128 x, int e) {
+  if (x.hi == 0 && x.lo == 0) return 0.0;
+  const int nbits = x.hi ? 128 - __clzll((long long)x.hi) : 64 - __clzll((long long)x.lo);
+  int ex = e + nbits - 1;  // exponent of the leading bit
+  unsigned long long mant;
+  if (nbits <= 53) {
+    mant = x.lo << (53 - nbits);
+  } else {
+    const int sh = nbits - 53;  // bits below the kept 53 (1..75)
+    mant = shr128(x, sh).lo;
+    const int hb = sh - 1;      // the half bit
+    const bool half = hb >= 64 ? ((x.hi >> (hb - 64)) & 1ull) : ((x.lo >> hb) & 1ull);
+    const bool sticky = hb >= 64 ? (x.lo != 0 || (x.hi & ((1ull << (hb - 64)) - 1ull)) != 0)
+                                 : (x.lo & ((1ull << hb) - 1ull)) != 0;
+    if (half && (sticky || (mant & 1ull))) {
+      ++mant;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++ex;
+      }
+    }
+  }
+  if (ex > 1023) return __longlong_as_double(0x7ff0000000000000ll);
+  const unsigned long long bits =
+      ((unsigned long long)(ex + 1023) << 52) | (mant & 0xfffffffffffffull);
+  return __longlong_as_double((long long)bits);
 }
 
 // ---------------------------------------------------------------------------

@@ -265,14 +265,17 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
     // ---- bound T = max a (exact, from the comparison copies)
     float Tf = 0.f;
     double T = 0.0;
+    bool zero;
     if constexpr (CMP == AR_CMP_F32) {
       const uint32_t tb = warp_max_u32(lmax);
       Tf = __uint_as_float(tb);
-      T = (double)Tf;
+      zero = tb == 0u;  // the maximum of non-negative copies, on bit patterns
     } else {
-      T = __longlong_as_double((long long)warp_max_u64(lmax64));
+      const unsigned long long tb = warp_max_u64(lmax64);
+      T = __longlong_as_double((long long)tb);
+      zero = tb == 0ull;
     }
-    if (T == 0.0) {
+    if (zero) {
       st |= AR_STATUS_ABSORBED;
       if (TIMED) record_until(p.t_end, true);  // the state holds to t_end
       break;

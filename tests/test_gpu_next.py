@@ -5,7 +5,7 @@
   ten runs of 10^7 selections, whose worst MSE falls inside the spread of
   that statistic under the rule's exact law, like the printed values (the
   printed errors are the rule's bias; see test_oracle_paper_rule.py).
-* ar_select_it (inverse transform, sequential FP64 running sums): indices and
+* ar_select_it (inverse transform, exact running sums by a parallel scan): indices and
   status bit-exact, including invalid and all-zero inputs.
 """
 import os
@@ -123,9 +123,25 @@ def test_inverse_transform_parity(gb, orc, make):
     assert int(st.item()) == ost
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_inverse_transform_parity_large(gb, orc, dtype):
+    """M = 2^20 (256 tiles of the scan, spread over 12 decades) and a ragged
+    M spanning several tiles: indices bit-exact with the oracle's exact
+    running sums."""
+    for M, K in ((1 << 20, 3000), (3 * 4096 + 1234, 20_000)):
+        a = W.wide_range(M, seed=40 + M).astype(dtype)
+        idx, st = gb.select_it(_t(a), K, seed=5, sel_offset=77)
+        oidx, ost = orc.select_it(a, K, seed=5, sel_offset=77, nthreads=8)
+        np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
+        assert int(st.item()) == ost == 0
+
+
 def test_inverse_transform_degenerate(gb, orc):
     for a in (np.zeros(7), np.zeros(0, np.float32), np.float32([1.0, np.nan, 2.0]),
-              np.array([1.0, -1.0, 3.0]), np.float32([np.inf, 1.0])):
+              np.array([1.0, -1.0, 3.0]), np.float32([np.inf, 1.0]),
+              np.float32([-0.0, 0.0, -0.0]), np.float32([-0.0, 2.0, 0.0]),
+              np.float32([3e20, 1e-30, 5.0, 1e-40]), np.array([1e308, 1e308, 5.0]),
+              np.array([1e-310, 3e-320, 0.0])):
         idx, st = gb.select_it(_t(a), 500, seed=4)
         oidx, ost = orc.select_it(a, 500, seed=4)
         np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
