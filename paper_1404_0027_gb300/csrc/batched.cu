@@ -61,18 +61,9 @@ constexpr int kBNT = kBWarps * 32;
 constexpr int kBCtasPerSm = 2;
 constexpr uint32_t kChunk = 1024;  // reduction chunk (elements)
 constexpr int kVPL = kChunk / 32;  // elements per lane (register path)
-#ifndef GBAR_RED_PREFETCH
-#define GBAR_RED_PREFETCH 0
-#endif
-#ifndef GBAR_SEL_ITEM
-#define GBAR_SEL_ITEM 64
-#endif
-#ifndef GBAR_SEL_U
-#define GBAR_SEL_U 3
-#endif
-constexpr uint32_t kSItem = GBAR_SEL_ITEM;  // selections per home work item
-constexpr uint32_t kGItem = GBAR_SEL_ITEM;  // selections per global-queue work item
-constexpr int kU = GBAR_SEL_U;              // Philox blocks per lane per round
+constexpr uint32_t kSItem = 64;     // selections per home work item
+constexpr uint32_t kGItem = 64;     // selections per global-queue work item
+constexpr int kU = 3;               // Philox blocks per lane per round
 
 // ---- plan-built work items -------------------------------------------------
 struct RItem {  // one reduction chunk: alpha_cat[e0, e0 + n)
@@ -409,21 +400,6 @@ __global__ void __launch_bounds__(kBNT, kBCtasPerSm) k_bound_reg(const Params p)
   const uint32_t* u = reinterpret_cast<const uint32_t*>(p.alpha);
   if (it >= p.nr) return;
   const uint32_t lane = threadIdx.x & 31u;
-#if GBAR_RED_PREFETCH
-  // Ask for every chunk of this warp at once (bulk prefetches into L2, no
-  // registers held, nothing waits for them): HBM streams the whole batch at
-  // full rate while the warps reduce, their own loads then hit L2.  Each
-  // prefetch covers a chunk's 16-byte groups only (aligned, inside alpha).
-  for (uint32_t q = it + lane * stride; q < p.nr; q += 32u * stride) {
-    const RItem d = p.ritems[q];
-    const int64_t g0 = (d.e0 + 3) & ~int64_t(3), g1 = (d.e0 + d.n) & ~int64_t(3);
-    if (g1 > g0) {
-      const uint32_t nbytes = (uint32_t)((g1 - g0) * 4);
-      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(u + g0), "r"(nbytes)
-                   : "memory");
-    }
-  }
-#endif
   auto load = [&](const RItem& d, uint32_t (&v)[kVPL], uint32_t& xs) -> int {
     int64_t g0 = (d.e0 + 3) & ~int64_t(3), g1 = (d.e0 + d.n) & ~int64_t(3);
     if (g1 < g0) g0 = g1 = d.e0;
