@@ -65,6 +65,9 @@ extern "C" {
 #define AR_STATUS_TRIAL_CAP 4u  /* a selection hit trial_cap; sentinel M   */
 #define AR_STATUS_BAD_BOUND 8u  /* bound NaN, inf, < 0 (or inf in FP32)    */
 #define AR_STATUS_ABSORBED 16u  /* SSA realization reached a0 = 0          */
+#define AR_STATUS_WAIT_LIMIT 32u  /* ar_select_batched, one-launch form: a bounded wait
+                                     for a realization's reduction gave up (not expected);
+                                     its selections are the sentinel M_b              */
 #define AR_STATUS_UNSUPPORTED 64u /* a batched realization with M_b >= 2^31 */
 #define AR_STATUS_T_END 128u      /* SSA realization reached its time limit    */
 
@@ -167,11 +170,16 @@ int ar_select_k(const void *d_alpha, int dtype, int64_t M, const double *d_bound
 /* ---------------------------------------------------------------------
  * ar_select_batched -- many realizations with uneven M_b and K_b:
  * ar_bound_batched followed by ar_select_batched_bounded with each
- * realization's own maximum as its bound, in two kernels enqueued on the
- * stream: the reduction, then the selections, which combine each
- * realization's chunk results themselves (Section "A GPU
- * acceptance-rejection algorithm": K realizations as K blocks; the text's
- * extension to M beyond one block).
+ * realization's own maximum as its bound (Section "A GPU acceptance-rejection
+ * algorithm": K realizations as K blocks; the text's extension to M beyond
+ * one block).  With a plan whose realizations all sit in CTA home lists
+ * (global share 0, the plan's default) and 16-byte aligned FP32 data, one
+ * kernel is enqueued: each persistent CTA reduces the chunks of its own
+ * realizations, then selects them (a bounded wait covers a realization
+ * still being reduced; past it AR_STATUS_WAIT_LIMIT is raised and that
+ * realization's indices are the sentinel -- not expected).  Otherwise two
+ * kernels: the reduction, then the selections, which combine each
+ * realization's chunk results themselves.  The results are the same.
  * Realization b owns alpha_cat[offsets[b] .. offsets[b+1]) and writes
  * K_b = out_offsets[b+1] - out_offsets[b] indices at d_idx[out_offsets[b]].
  * Its bound is its own maximum, computed in the kernel; its Philox
@@ -251,9 +259,11 @@ int ar_select_batched_bounded(const void *d_alpha_cat, int dtype, const int64_t 
  *     realizations (estimated cost K_b (0.6 + ln M_b) + 0.05 M_b) are
  *     assigned to the persistent CTAs of the selection kernel by
  *     longest-processing-time-first list scheduling (each CTA's home list);
- *     the cheapest ones, 30% of the estimated cost by default, form a
- *     global queue that balances the CTAs' finishing times (40 bytes per
- *     range).  Default tile: 16 warps per CTA, 2 CTAs per SM;
+ *     the cheapest ones, a chosen share of the estimated cost, may form a
+ *     global queue that balances the CTAs' finishing times (48 bytes per
+ *     range; each CTA's list of chunks to reduce comes with the one-launch
+ *     form).  Default tile: 32 warps per CTA (one CTA per SM) with no
+ *     global queue, which makes ar_select_batched one launch for FP32 data;
  *     ar_plan_autotune picks tile and share on the caller's data;
  *   - device scratch for the chunk partials (32 bytes per chunk).
  * Results are identical with or without a plan.  Calls sharing a plan must

@@ -31,6 +31,7 @@ AR_STATUS_ALL_ZERO = 2
 AR_STATUS_TRIAL_CAP = 4
 AR_STATUS_BAD_BOUND = 8
 AR_STATUS_ABSORBED = 16
+AR_STATUS_WAIT_LIMIT = 32
 AR_STATUS_UNSUPPORTED = 64
 
 AR_F32 = 0

@@ -4,14 +4,18 @@
 // "Implementation"; several blocks per realization when M exceeds a block,
 // Discussion).
 //
-// ar_select_batched is two launches on the caller's stream, the reduction
-// and the selections (ar_bound_batched: the reduction and the combine):
+// With a plan whose realizations all sit in CTA home lists (global share 0,
+// the default) and 16-byte aligned FP32 data, ar_select_batched is ONE launch
+// of k_batched_select<..., FUSED>: each CTA first reduces the chunks of its
+// own home realizations, then selects them (see the kernel).  Otherwise it is
+// two launches on the caller's stream, the reduction and the selections
+// (ar_bound_batched: the reduction and the combine):
 //
 //   k_bound_reg / k_batched_bound   per-chunk partial results: maximum
 //       (exact, on bit patterns), validity and exact sum of chunks of at most
 //       1024 propensities (with a plan: each realization cut into equal
-//       chunks).  Each warp streams its chunks with 16-byte vector loads into
-//       registers, one chunk ahead of the one it reduces, and only touches
+//       chunks).  Each warp loads its chunk with 16-byte vector loads into
+//       registers (one chunk in flight per warp, 32 warps per SM), and only touches
 //       the 16-byte groups a chunk has.  A chunk's sum is an exact integer in
 //       units of a power of two set by the chunk's maximum: when every
 //       non-zero value lies within 2^24 of that maximum (the common case) it
@@ -58,7 +62,7 @@ constexpr int kSelShapes[3] = {16, 32, 8};
 constexpr int kSelThreadsPerSm = 1024;
 constexpr int kBWarps = 8;  // reduction kernels
 constexpr int kBNT = kBWarps * 32;
-constexpr int kBCtasPerSm = 2;
+constexpr int kBCtasPerSm = 4;  // k_bound_reg: 32 warps per SM, 64 registers
 constexpr uint32_t kChunk = 1024;  // reduction chunk (elements)
 constexpr int kVPL = kChunk / 32;  // elements per lane (register path)
 constexpr uint32_t kSItem = 64;     // selections per home work item
@@ -78,6 +82,8 @@ struct SItem {     // selections [s0, s1) of realization b
   int64_t a0, o0;  // first element / first output index of the realization
   uint32_t M, b, s0, s1;
   uint32_t p0, nch;  // its chunk partials
+  uint32_t slot;     // the realization's place in its CTA's home list (fused launch)
+  uint32_t pad;
 };
 struct Part {                 // a chunk's partial result
   unsigned long long hi, lo;  // FP32 data: exact sum (hi:lo) 2^e; FP64: lo = sum bits
@@ -94,6 +100,8 @@ struct Scratch {
 };
 
 struct Params {
+  const uint2* fred;     // fused launch: the chunks each CTA reduces, (chunk, slot)
+  const uint32_t* frptr; // [grid + 1] fused launch: a CTA's range of fred
   const RItem* ritems;   // NULL: one item per realization, read from the offsets
   const RInfo* rinfo;    // [B] (plan)
   const SItem* sitems;   // NULL: one item per realization, global queue
@@ -122,6 +130,7 @@ struct Params {
   int64_t bound_stride;
   uint32_t bound_given;  // caller's bounds: checked like ar_select_k's
   uint32_t zero_status;  // the reduction reports all-zero realizations
+  uint32_t nslots;       // fused launch: shared-memory counters per CTA (home realizations)
   uint32_t fold;         // the selection takes T from the chunk partials and the
                          // first range of a realization writes {T, sum}, status
 };
@@ -394,54 +403,38 @@ __device__ __forceinline__ Part reduce_f32q(const uint32_t (&v)[N], uint32_t xs,
   return reduce_f32<N>(v, xs);  // slow path (zeros beyond kq are loaded as zeros)
 }
 
+// Reduces chunk c of the plan (16-byte loads straight into lane registers)
+// and stores its partial result.
+__device__ __forceinline__ void reduce_chunk(const Params& p, uint32_t c) {
+  const uint32_t* u = reinterpret_cast<const uint32_t*>(p.alpha);
+  const uint32_t lane = threadIdx.x & 31u;
+  const RItem d = p.ritems[c];
+  int64_t g0 = (d.e0 + 3) & ~int64_t(3), g1 = (d.e0 + d.n) & ~int64_t(3);
+  if (g1 < g0) g0 = g1 = d.e0;
+  const uint32_t ngroups = (uint32_t)((g1 - g0) >> 2);
+  const int kq = (int)((ngroups + 31u) >> 5);
+  const uint4* gp = reinterpret_cast<const uint4*>(u + g0);
+  uint32_t v[kVPL];
+#pragma unroll
+  for (int k = 0; k < kVPL / 4; ++k) {
+    const uint32_t g = lane + 32u * k;
+    uint4 x = make_uint4(0u, 0u, 0u, 0u);
+    if (k < kq && g < ngroups) x = __ldg(gp + g);
+    v[4 * k] = x.x; v[4 * k + 1] = x.y; v[4 * k + 2] = x.z; v[4 * k + 3] = x.w;
+  }
+  const int64_t hn = g0 - d.e0, tn = d.e0 + d.n - g1;
+  uint32_t xs = 0u;
+  if (lane < 3 && (int64_t)lane < hn) xs = __ldg(u + d.e0 + lane);
+  else if (lane >= 3 && lane < 6 && (int64_t)(lane - 3) < tn) xs = __ldg(u + g1 + (lane - 3));
+  store_part(p.parts + c, reduce_f32q<kVPL>(v, xs, kq));
+}
+
+// One chunk in flight per warp, 32 warps per SM: more warps to cover the
+// loads' latency and the reduce work than two chunks per warp at 16 warps.
 __global__ void __launch_bounds__(kBNT, kBCtasPerSm) k_bound_reg(const Params p) {
   const uint32_t stride = gridDim.x * kBWarps;
-  uint32_t it = blockIdx.x * kBWarps + (threadIdx.x >> 5);
-  const uint32_t* u = reinterpret_cast<const uint32_t*>(p.alpha);
-  if (it >= p.nr) return;
-  const uint32_t lane = threadIdx.x & 31u;
-  auto load = [&](const RItem& d, uint32_t (&v)[kVPL], uint32_t& xs) -> int {
-    int64_t g0 = (d.e0 + 3) & ~int64_t(3), g1 = (d.e0 + d.n) & ~int64_t(3);
-    if (g1 < g0) g0 = g1 = d.e0;
-    const uint32_t ngroups = (uint32_t)((g1 - g0) >> 2);
-    const int kq = (int)((ngroups + 31u) >> 5);
-    const uint4* gp = reinterpret_cast<const uint4*>(u + g0);
-#pragma unroll
-    for (int k = 0; k < kVPL / 4; ++k) {
-      const uint32_t g = lane + 32u * k;
-      uint4 x = make_uint4(0u, 0u, 0u, 0u);
-      if (k < kq && g < ngroups) x = __ldg(gp + g);
-      v[4 * k] = x.x; v[4 * k + 1] = x.y; v[4 * k + 2] = x.z; v[4 * k + 3] = x.w;
-    }
-    const int64_t hn = g0 - d.e0, tn = d.e0 + d.n - g1;
-    xs = 0u;
-    if (lane < 3 && (int64_t)lane < hn) xs = __ldg(u + d.e0 + lane);
-    else if (lane >= 3 && lane < 6 && (int64_t)(lane - 3) < tn) xs = __ldg(u + g1 + (lane - 3));
-    return kq;
-  };
-  uint32_t va[kVPL], vb[kVPL], xa, xb;
-  int qa, qb = 0;
-  RItem d = p.ritems[it];
-  qa = load(d, va, xa);
-  if (it + stride < p.nr) d = p.ritems[it + stride];
-  for (;;) {
-    uint32_t nx = it + stride;
-    if (nx < p.nr) {
-      qb = load(d, vb, xb);
-      if (nx + stride < p.nr) d = p.ritems[nx + stride];
-    }
-    store_part(p.parts + it, reduce_f32q<kVPL>(va, xa, qa));
-    if (nx >= p.nr) return;
-    it = nx;
-    nx = it + stride;
-    if (nx < p.nr) {
-      qa = load(d, va, xa);
-      if (nx + stride < p.nr) d = p.ritems[nx + stride];
-    }
-    store_part(p.parts + it, reduce_f32q<kVPL>(vb, xb, qb));
-    if (nx >= p.nr) return;
-    it = nx;
-  }
+  for (uint32_t it = blockIdx.x * kBWarps + (threadIdx.x >> 5); it < p.nr; it += stride)
+    reduce_chunk(p, it);
 }
 
 // Register path: FP64 data, unaligned FP32 buffers, calls without a plan.
@@ -656,16 +649,29 @@ struct Claimer {
 // Claims the next selection item and gathers what the warp needs about it;
 // returns false when no work is left.  Realizations whose bound is unusable
 // get their indices set to M here and are skipped.
-template <typename TS, int CMP>
+// Fused launch: how long a warp waits for the reduction of a realization its
+// CTA is still reducing (it never waits in practice: every chunk of the
+// realization was claimed before any of its selection ranges, by warps that
+// reduce it without waiting).  Past the limit the realization's selections
+// get the sentinel and AR_STATUS_WAIT_LIMIT is raised.
+constexpr uint32_t kFusedWaitLimit = 1u << 22;
+
+template <typename TS, int CMP, bool FUSED = false>
 __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Claimer& cl,
-                          WItem<TS, CMP>& w, uint32_t& st_acc) {
+                          WItem<TS, CMP>& w, uint32_t& st_acc, uint32_t* pre = nullptr,
+                          const uint32_t* s_done = nullptr) {
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
     uint32_t i = 0;
     bool ok = false;
     if (p.sitems && cl.home) {
-      if (lane == 0) i = atomicAdd(s_queue, 1u);
-      i = __shfl_sync(kFull, i, 0);
+      if (FUSED && *pre != 0xffffffffu) {  // the range the warp claimed when it left
+        i = *pre;                          // the reduction phase
+        *pre = 0xffffffffu;
+      } else {
+        if (lane == 0) i = atomicAdd(s_queue, 1u);
+        i = __shfl_sync(kFull, i, 0);
+      }
       ok = i < q_end;
       if (!ok) cl.home = false;
     }
@@ -684,7 +690,7 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
       if (i >= qe) return false;
     }
     int64_t a0 = 0, o0 = 0;
-    uint32_t M = 0, b = 0, s0 = 0, s1 = 0, p0 = 0, nch = 1;
+    uint32_t M = 0, b = 0, s0 = 0, s1 = 0, p0 = 0, nch = 1, slot = 0;
     if (p.sitems) {
       const SItem& si = p.sitems[i];
       a0 = si.a0;
@@ -695,6 +701,7 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
       s1 = si.s1;
       p0 = si.p0;
       nch = si.nch;
+      slot = si.slot;
     } else {
       b = i;
       p0 = i;
@@ -716,6 +723,25 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
     // their checks need no FP64 operation (GB300's FP64 pipe is narrow).
     BoundT<CMP> Tc = 0;
     uint32_t st = 0;
+    if constexpr (FUSED) {
+      // wait until this CTA has reduced every chunk of the realization
+      const volatile uint32_t* done = s_done + slot;
+      uint32_t spins = 0;
+      while (*done < nch && spins < kFusedWaitLimit) {
+        __nanosleep(64);
+        ++spins;
+      }
+      __syncwarp();
+      // pairs with the reducing warp's fence: its chunk partials, read below
+      // through this SM's L1 (the CTA's point of coherence), are visible
+      __threadfence_block();
+      if (spins >= kFusedWaitLimit) {
+        st_acc |= AR_STATUS_WAIT_LIMIT;
+        int32_t* out = p.idx + o0;
+        for (uint32_t k = s0 + lane; k < s1; k += 32) out[k] = (int32_t)M;
+        continue;
+      }
+    }
     if (p.fold) {
       unsigned long long vm;
       uint32_t bd;
@@ -765,26 +791,62 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
   }
 }
 
-template <typename TS, int CMP, int NW>
+// FUSED: one launch for the whole call (FP32 data with a plan whose
+// realizations all sit in CTA home lists).  Each CTA first reduces the chunks
+// of its own home realizations (every warp claims chunks from a shared
+// counter; a chunk's partial goes to global memory, then the realization's
+// count of reduced chunks in shared memory is raised), then the warps go on
+// to the selections exactly as in the two-launch call, taking a
+// realization's bound once all its chunks are counted.  Chunks are claimed
+// before any selection range, in home-list order, from the same counter.
+template <typename TS, int CMP, int NW, bool FUSED = false>
 __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
     k_batched_select(const Params p) {
   __shared__ uint32_t s_scr[NW * 64];
   __shared__ uint32_t s_queue;
+  extern __shared__ uint32_t s_done[];  // fused: reduced chunks per home realization
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t lt = (1u << lane) - 1u;
   uint32_t* scr = s_scr + (threadIdx.x >> 5) * 64;
   uint32_t q_end = 0;
+  uint32_t nred = 0, r0 = 0;
+  if constexpr (FUSED) {
+    r0 = p.frptr[blockIdx.x];
+    nred = p.frptr[blockIdx.x + 1] - r0;
+    for (uint32_t k = threadIdx.x; k < p.nslots; k += blockDim.x) s_done[k] = 0u;
+  }
   if (p.sitems) {
-    if (threadIdx.x == 0) s_queue = p.scta[blockIdx.x];
+    // fused: the counter starts nred below the first home range, so its
+    // first nred values name chunks and the rest are home ranges
+    if (threadIdx.x == 0) s_queue = p.scta[blockIdx.x] - nred;
     q_end = p.scta[blockIdx.x + 1];
   }
   __syncthreads();
+  uint32_t pre = 0xffffffffu;
+  if constexpr (FUSED) {
+    const uint32_t base = p.scta[blockIdx.x] - nred;
+    for (;;) {
+      uint32_t i = 0;
+      if (lane == 0) i = atomicAdd(&s_queue, 1u);
+      i = __shfl_sync(kFull, i, 0);
+      const uint32_t k = i - base;
+      if (k >= nred) {
+        pre = i;  // the warp's first selection range
+        break;
+      }
+      const uint2 fr = p.fred[r0 + k];  // (chunk, slot)
+      reduce_chunk(p, fr.x);
+      __syncwarp();
+      __threadfence_block();  // the partial is visible to the CTA before the count
+      if (lane == 0) atomicAdd(s_done + fr.y, 1u);
+    }
+  }
   SelCounters cnt;
   uint32_t st_acc = 0;
   Lane<TS, CMP> L;
   WItem<TS, CMP> cur;
   Claimer cl;
-  bool have = next_item<TS, CMP>(p, &s_queue, q_end, cl, cur, st_acc);
+  bool have = next_item<TS, CMP, FUSED>(p, &s_queue, q_end, cl, cur, st_acc, &pre, s_done);
   bool tail = false;
   for (;;) {
     // ---- refill idle lanes from the current item (claiming the next one
@@ -806,7 +868,8 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
         }
         const uint32_t ni = __popc(idle);
         cur.s += ni < avail ? ni : avail;
-        if (cur.s == cur.s1) have = next_item<TS, CMP>(p, &s_queue, q_end, cl, cur, st_acc);
+        if (cur.s == cur.s1)
+          have = next_item<TS, CMP, FUSED>(p, &s_queue, q_end, cl, cur, st_acc, &pre, s_done);
         idle = __ballot_sync(kFull, !L.act);
       }
     }
@@ -955,6 +1018,17 @@ int launch_select(const Params& p, uint32_t sel_grid, int shape, cudaStream_t s)
   return check_launch();
 }
 
+// The one-launch call (FP32 data, plan with every realization in a home list).
+template <int CMP>
+int launch_fused(const Params& p, uint32_t sel_grid, int shape, cudaStream_t s) {
+  const int nw = kSelShapes[shape];
+  const size_t smem = sizeof(uint32_t) * p.nslots;
+  if (nw == 32) k_batched_select<float, CMP, 32, true><<<sel_grid, 32 * 32, smem, s>>>(p);
+  else if (nw == 8) k_batched_select<float, CMP, 8, true><<<sel_grid, 8 * 32, smem, s>>>(p);
+  else k_batched_select<float, CMP, 16, true><<<sel_grid, 16 * 32, smem, s>>>(p);
+  return check_launch();
+}
+
 }  // namespace
 }  // namespace gbar
 
@@ -975,6 +1049,12 @@ struct ar_plan {
   size_t sitems_cap;    // SItem capacity of d_sitems
   uint32_t* d_scta;
   size_t scta_cap;
+  // one-launch (fused) form, when every realization sits in a home list: the
+  // chunks each CTA reduces, (chunk, slot), and each CTA's range of them
+  uint2* d_fred;
+  uint32_t* d_frptr;
+  uint32_t nslots;  // the longest home list, in realizations
+  bool fused;
   unsigned char* d_scratch;  // Scratch | parts[NR]
   std::vector<int64_t> off, oo;  // host copies of the offsets (schedule rebuilds)
   std::vector<double> cost;
@@ -1073,10 +1153,42 @@ int set_schedule(ar_plan& pl, int shape, int gshare_pm) {
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(pl.d_scta, scta.data(), sizeof(uint32_t) * scta.size(), cudaMemcpyHostToDevice);
+  // the one-launch form: each CTA reduces the chunks of its own home
+  // realizations (in home-list order) before selecting them
+  const bool fused = gq0 == (uint32_t)sitems.size();
+  uint32_t nslots = 0;
+  if (e == cudaSuccess && fused) {
+    std::vector<uint2> fred;
+    std::vector<uint32_t> frptr(grid + 1, 0);
+    fred.reserve(pl.nr);
+    for (uint32_t c = 0; c < grid; ++c) {
+      uint32_t slot = 0;
+      for (uint32_t k = scta[c]; k < scta[c + 1]; ++k) {
+        if (k > scta[c] && sitems[k].b != sitems[k - 1].b) ++slot;
+        sitems[k].slot = slot;
+        if (sitems[k].s0 == 0)
+          for (uint32_t q = 0; q < sitems[k].nch; ++q) fred.push_back(make_uint2(sitems[k].p0 + q, slot));
+      }
+      if (scta[c + 1] > scta[c]) nslots = std::max(nslots, slot + 1);
+      frptr[c + 1] = (uint32_t)fred.size();
+    }
+    if (!pl.d_fred) e = cudaMalloc(&pl.d_fred, sizeof(uint2) * std::max<size_t>(pl.nr, 1));
+    if (e == cudaSuccess && !pl.d_frptr) e = cudaMalloc(&pl.d_frptr, sizeof(uint32_t) * pl.scta_cap);
+    if (e == cudaSuccess && !fred.empty())
+      e = cudaMemcpy(pl.d_fred, fred.data(), sizeof(uint2) * fred.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(pl.d_frptr, frptr.data(), sizeof(uint32_t) * frptr.size(),
+                     cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)  // the slots were set after the first upload
+      e = cudaMemcpy(pl.d_sitems, sitems.data(), sizeof(SItem) * sitems.size(),
+                     cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     set_cuda_error(e);
     return AR_ERR_CUDA;
   }
+  pl.fused = fused && nslots > 0;
+  pl.nslots = nslots;
   pl.ns = (uint32_t)sitems.size();
   pl.gq0 = gq0;
   pl.grid = grid;
@@ -1090,6 +1202,8 @@ void free_plan(ar_plan* p) {
   cudaFree(p->d_rinfo);
   cudaFree(p->d_sitems);
   cudaFree(p->d_scta);
+  cudaFree(p->d_fred);
+  cudaFree(p->d_frptr);
   cudaFree(p->d_scratch);
   delete p;
 }
@@ -1162,7 +1276,9 @@ extern "C" int ar_plan_create(const int64_t* h_offsets, const int64_t* h_out_off
     free_plan(p);
     return AR_ERR_CUDA;
   }
-  const int rc = set_schedule(*p, 0, 300);  // default: 16 warps per CTA, 30 % global queue
+  // default: 32 warps per CTA, every realization in a home list (the one-launch
+  // form of ar_select_batched for FP32 data)
+  const int rc = set_schedule(*p, 1, 0);
   if (rc) {
     free_plan(p);
     return rc;
@@ -1219,6 +1335,11 @@ int batched_params(const void* d_alpha_cat, int dtype, const int64_t* d_offsets,
     sel_grid = plan->grid;
     shape = plan->shape;
     stream_path = dtype == AR_F32 && p.vec_ok;
+    if (plan->fused) {
+      p.fred = plan->d_fred;
+      p.frptr = plan->d_frptr;
+      p.nslots = plan->nslots;
+    }
   } else {
     if (!d_work || work_bytes < ar_select_batched_workspace_size(B)) return AR_ERR_WORKSPACE;
     if (!aligned(d_work, 16)) return AR_ERR_ALIGN;
@@ -1333,6 +1454,10 @@ extern "C" int ar_select_batched(const void* d_alpha_cat, int dtype, const int64
   p.bound_sum = d_bound_sum;
   p.fold = 1u;  // the selection kernel combines the chunk partials itself
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (stream_path && p.fred) {  // one launch: each CTA reduces its own realizations
+    return cmp == AR_CMP_F32 ? launch_fused<AR_CMP_F32>(p, sel_grid, shape, s)
+                             : launch_fused<AR_CMP_F64>(p, sel_grid, shape, s);
+  }
   rc = dtype == AR_F32 ? launch_bound<float>(p, stream_path, false, s)
                        : launch_bound<double>(p, stream_path, false, s);
   if (rc) return rc;

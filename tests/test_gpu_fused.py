@@ -1,0 +1,124 @@
+"""GPU parity of the one-launch form of ar_select_batched (FP32 data with a
+plan whose realizations all sit in CTA home lists, global share 0): each CTA
+reduces the chunks of its own realizations, then selects them.  The results
+must be exactly those of the oracle (and of the two-launch form): indices,
+counters and maxima bit-exact, totals within the FP64 bound, status bits."""
+import numpy as np
+import pytest
+
+from paper_1404_0027_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    from paper_1404_0027_gb300 import build
+    build.build()
+    from paper_1404_0027_gb300 import binding
+    binding.lib()
+    assert torch.cuda.is_available()
+    return binding
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _check(gb, orc, bt, warps, cmp=0, seed=1, sel_offset=0, realization_base=0,
+           trial_cap=1 << 20, status=None):
+    plan = gb.Plan(bt.offsets, bt.out_offsets)
+    gb.ar_plan_set_tile(plan, warps, 0)   # every realization in a home list: one launch
+    bs, idx, stats, st = gb.select_batched(_t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets),
+                                           seed=seed, sel_offset=sel_offset,
+                                           realization_base=realization_base, cmp=cmp,
+                                           trial_cap=trial_cap, plan=plan)
+    obs, oidx, ostats, ost = orc.select_batched(bt, seed=seed, sel_offset=sel_offset,
+                                                realization_base=realization_base, cmp=cmp,
+                                                trial_cap=trial_cap, nthreads=8)
+    g = idx.cpu().numpy()
+    mism = np.flatnonzero(g != oidx)
+    assert mism.size == 0, f"{mism.size} mismatches of {g.size}, first at {mism[:5]}"
+    np.testing.assert_array_equal(stats.cpu().numpy().astype(np.uint64), ostats)
+    gbs = bs.cpu().numpy()
+    np.testing.assert_array_equal(np.isnan(gbs), np.isnan(obs))
+    ok = ~np.isnan(obs[:, 0])
+    np.testing.assert_array_equal(gbs[ok, 0], obs[ok, 0])
+    for b in np.flatnonzero(ok):
+        a = bt.alpha[bt.offsets[b]:bt.offsets[b + 1]]
+        assert abs(gbs[b, 1] - obs[b, 1]) <= 2.0 * (a.size + 8) * 2.0 ** -53 * abs(obs[b, 1]), b
+    assert int(st.item()) == ost
+    if status is not None:
+        assert ost == status
+    plan.close()
+
+
+@pytest.mark.parametrize("warps", [8, 16, 32])
+def test_fused_full_workload(gb, orc, warps):
+    """The benchmark's batch: 4096 realizations, M_b log-uniform in [64, 16384]."""
+    _check(gb, orc, W.batched_uneven(seed=302), warps)
+
+
+@pytest.mark.parametrize("warps", [8, 32])
+@pytest.mark.parametrize("cmp", [0, 1])
+def test_fused_ragged(gb, orc, warps, cmp):
+    """Empty realizations (M_b = 0), realizations without selections
+    (K_b = 0), all-zero propensities, realizations of one chunk and of many,
+    offsets not on 16-byte boundaries inside the batch."""
+    vecs = [W.skewed(m, seed=m).astype(np.float32) for m in (1, 2, 3, 5, 7, 64, 1000, 4099,
+                                                               16384, 20_000, 9, 1)]
+    vecs.insert(4, np.zeros(0, dtype=np.float32))
+    vecs.append(np.zeros(33, dtype=np.float32))
+    ks = [5, 0, 17, 1, 7, 256, 300, 256, 1000, 64, 77, 3, 2, 9]
+    _check(gb, orc, W.batch_from_vectors(vecs, ks), warps, cmp=cmp, seed=7, sel_offset=11,
+           realization_base=100)
+
+
+@pytest.mark.parametrize("warps", [8, 32])
+def test_fused_invalid_realizations(gb, orc, warps):
+    """NaN, negative and infinite propensities in three realizations:
+    BAD_ALPHA, (NaN, NaN) bounds and the sentinel there, the others exact."""
+    bt = W.batched_uneven(B=400, seed=308, m_lo=16, m_hi=5000, K=40)
+    a = bt.alpha.copy()
+    a[bt.offsets[5] + 2] = np.nan
+    a[bt.offsets[17]] = -1.0
+    a[bt.offsets[390] + 1] = np.inf
+    _check(gb, orc, W.Batch(a, bt.offsets, bt.out_offsets), warps,
+           status=gb.AR_STATUS_BAD_ALPHA)
+
+
+@pytest.mark.parametrize("cap", [1, 2, 7])
+def test_fused_trial_cap(gb, orc, cap):
+    _check(gb, orc, W.batched_uneven(B=200, seed=309, K=64), 16, trial_cap=cap,
+           status=gb.AR_STATUS_TRIAL_CAP)
+
+
+def test_fused_graph_replays(gb, orc):
+    """One launch per call replayed from a CUDA graph: every replay gives the
+    same indices and the counters add up (the launch leaves no state behind)."""
+    import torch
+    bt = W.batched_uneven(B=1200, seed=310, K=96)
+    plan = gb.Plan(bt.offsets, bt.out_offsets)
+    gb.ar_plan_set_tile(plan, 32, 0)
+    a, off, oo = _t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets)
+    bs = torch.empty((bt.B, 2), dtype=torch.float64, device="cuda")
+    idx = torch.empty(int(bt.out_offsets[-1]), dtype=torch.int32, device="cuda")
+    stats = torch.zeros(3, dtype=torch.int64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        gb.ar_select_batched(a, off, oo, 1, 0, 0, 0, 1 << 20, plan, bs, idx, stats, st, None, s)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        gb.ar_select_batched(a, off, oo, 1, 0, 0, 0, 1 << 20, plan, bs, idx, stats, st, None, s)
+    for _ in range(7):
+        g.replay()
+    torch.cuda.synchronize()
+    obs, oidx, ostats, ost = orc.select_batched(bt, nthreads=8)
+    np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
+    np.testing.assert_array_equal(stats.cpu().numpy().astype(np.uint64), 8 * ostats)
+    assert int(st.item()) == ost
+    plan.close()
