@@ -623,7 +623,9 @@ def main():
     roofline_alu = {"bound": "alu", "achieved": blocks_per_launch / sel_s, "peak": alu_peak,
                     "unit": "Philox4x32-10 blocks/s",
                     "frac": blocks_per_launch / sel_s / alu_peak,
-                    "traffic": profiled_traffic("k_batched_select_batched_uneven.md"),
+                    # this kernel's own live traffic was not captured on these
+                    # sources (the capture covers the one-launch call)
+                    "traffic": None,
                     "kernel": "k_batched_select<float, AR_CMP_F32> (ar_select_batched_bounded)",
                     "peak_from": f"{IMAD_PER_SM_CLK} IMAD/clk/SM x {sm_count} SMs x "
                                  f"{clk:.0f} MHz / {PHILOX_IMAD_PER_BLOCK} IMAD per block",
