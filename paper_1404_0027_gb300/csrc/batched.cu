@@ -655,6 +655,9 @@ struct Claimer {
 // reduce it without waiting).  Past the limit the realization's selections
 // get the sentinel and AR_STATUS_WAIT_LIMIT is raised.
 constexpr uint32_t kFusedWaitLimit = 1u << 22;
+// the one-launch form keeps one 32-bit count per home realization of a CTA in
+// dynamic shared memory; longer home lists take the two-launch form
+constexpr uint32_t kMaxFusedSlots = 8192;
 
 template <typename TS, int CMP, bool FUSED = false>
 __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Claimer& cl,
@@ -1187,7 +1190,9 @@ int set_schedule(ar_plan& pl, int shape, int gshare_pm) {
     set_cuda_error(e);
     return AR_ERR_CUDA;
   }
-  pl.fused = fused && nslots > 0;
+  // the counters live in dynamic shared memory beside the kernel's own 8 KB:
+  // beyond kMaxFusedSlots home realizations per CTA the call takes two launches
+  pl.fused = fused && nslots > 0 && nslots <= kMaxFusedSlots;
   pl.nslots = nslots;
   pl.ns = (uint32_t)sitems.size();
   pl.gq0 = gq0;
