@@ -173,8 +173,8 @@ int ar_select_k(const void *d_alpha, int dtype, int64_t M, const double *d_bound
  * realization's own maximum as its bound (Section "A GPU acceptance-rejection
  * algorithm": K realizations as K blocks; the text's extension to M beyond
  * one block).  With a plan whose realizations all sit in CTA home lists
- * (global share 0, the plan's default) and 16-byte aligned FP32 data, one
- * kernel is enqueued: each persistent CTA reduces the chunks of its own
+ * (global share 0, the plan's default; at most 4096 per CTA) and 16-byte
+ * aligned FP32 data, one kernel is enqueued: each persistent CTA reduces the chunks of its own
  * realizations, then selects them (a bounded wait covers a realization
  * still being reduced; past it AR_STATUS_WAIT_LIMIT is raised and that
  * realization's indices are the sentinel -- not expected).  Otherwise two

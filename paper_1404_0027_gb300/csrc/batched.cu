@@ -405,7 +405,7 @@ __device__ __forceinline__ Part reduce_f32q(const uint32_t (&v)[N], uint32_t xs,
 
 // Reduces chunk c of the plan (16-byte loads straight into lane registers)
 // and stores its partial result.
-__device__ __forceinline__ void reduce_chunk(const Params& p, uint32_t c) {
+__device__ __forceinline__ Part reduce_chunk(const Params& p, uint32_t c) {
   const uint32_t* u = reinterpret_cast<const uint32_t*>(p.alpha);
   const uint32_t lane = threadIdx.x & 31u;
   const RItem d = p.ritems[c];
@@ -426,7 +426,9 @@ __device__ __forceinline__ void reduce_chunk(const Params& p, uint32_t c) {
   uint32_t xs = 0u;
   if (lane < 3 && (int64_t)lane < hn) xs = __ldg(u + d.e0 + lane);
   else if (lane >= 3 && lane < 6 && (int64_t)(lane - 3) < tn) xs = __ldg(u + g1 + (lane - 3));
-  store_part(p.parts + c, reduce_f32q<kVPL>(v, xs, kq));
+  const Part r = reduce_f32q<kVPL>(v, xs, kq);
+  store_part(p.parts + c, r);
+  return r;
 }
 
 // One chunk in flight per warp, 32 warps per SM: more warps to cover the
@@ -655,14 +657,16 @@ struct Claimer {
 // reduce it without waiting).  Past the limit the realization's selections
 // get the sentinel and AR_STATUS_WAIT_LIMIT is raised.
 constexpr uint32_t kFusedWaitLimit = 1u << 22;
-// the one-launch form keeps one 32-bit count per home realization of a CTA in
-// dynamic shared memory; longer home lists take the two-launch form
-constexpr uint32_t kMaxFusedSlots = 8192;
+// the one-launch form keeps two 32-bit words per home realization of a CTA in
+// dynamic shared memory (its reduced-chunk count and its maximum): up to
+// 32 KB beside the kernel's 8 KB, under the 48 KB a launch gets without
+// opting in; longer home lists take the two-launch form
+constexpr uint32_t kMaxFusedSlots = 4096;
 
 template <typename TS, int CMP, bool FUSED = false>
 __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Claimer& cl,
                           WItem<TS, CMP>& w, uint32_t& st_acc, uint32_t* pre = nullptr,
-                          const uint32_t* s_done = nullptr) {
+                          const uint32_t* s_done = nullptr, const uint32_t* s_tmax = nullptr) {
   const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
     uint32_t i = 0;
@@ -745,7 +749,14 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
         continue;
       }
     }
-    if (p.fold) {
+    if (FUSED && s0 != 0) {
+      // fused, not the realization's first range: its maximum is in shared
+      // memory (the first range reduces the chunk partials: it writes the sum)
+      const uint32_t tb = s_tmax[slot];
+      if (tb == 0xffffffffu) st = 1;
+      else if (tb == 0u || M == 0) st = AR_STATUS_ALL_ZERO;
+      else Tc = (BoundT<CMP>)__uint_as_float(tb);
+    } else if (p.fold) {
       unsigned long long vm;
       uint32_t bd;
       realization_bound<TS>(p, p0, nch, b, s0 == 0, vm, bd, st_acc);
@@ -813,10 +824,11 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
   uint32_t* scr = s_scr + (threadIdx.x >> 5) * 64;
   uint32_t q_end = 0;
   uint32_t nred = 0, r0 = 0;
+  uint32_t* s_tmax = s_done + p.nslots;  // fused: maximum per home realization
   if constexpr (FUSED) {
     r0 = p.frptr[blockIdx.x];
     nred = p.frptr[blockIdx.x + 1] - r0;
-    for (uint32_t k = threadIdx.x; k < p.nslots; k += blockDim.x) s_done[k] = 0u;
+    for (uint32_t k = threadIdx.x; k < 2u * p.nslots; k += blockDim.x) s_done[k] = 0u;
   }
   if (p.sitems) {
     // fused: the counter starts nred below the first home range, so its
@@ -838,9 +850,11 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
         break;
       }
       const uint2 fr = p.fred[r0 + k];  // (chunk, slot)
-      reduce_chunk(p, fr.x);
+      const Part part = reduce_chunk(p, fr.x);
+      // the realization's maximum (bit pattern; all ones: an invalid value)
+      if (lane == 0) atomicMax(s_tmax + fr.y, part.bad ? 0xffffffffu : (uint32_t)part.vmax);
       __syncwarp();
-      __threadfence_block();  // the partial is visible to the CTA before the count
+      __threadfence_block();  // the partial and the maximum are visible before the count
       if (lane == 0) atomicAdd(s_done + fr.y, 1u);
     }
   }
@@ -849,7 +863,7 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
   Lane<TS, CMP> L;
   WItem<TS, CMP> cur;
   Claimer cl;
-  bool have = next_item<TS, CMP, FUSED>(p, &s_queue, q_end, cl, cur, st_acc, &pre, s_done);
+  bool have = next_item<TS, CMP, FUSED>(p, &s_queue, q_end, cl, cur, st_acc, &pre, s_done, s_tmax);
   bool tail = false;
   for (;;) {
     // ---- refill idle lanes from the current item (claiming the next one
@@ -872,7 +886,8 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
         const uint32_t ni = __popc(idle);
         cur.s += ni < avail ? ni : avail;
         if (cur.s == cur.s1)
-          have = next_item<TS, CMP, FUSED>(p, &s_queue, q_end, cl, cur, st_acc, &pre, s_done);
+          have = next_item<TS, CMP, FUSED>(p, &s_queue, q_end, cl, cur, st_acc, &pre, s_done,
+                                           s_tmax);
         idle = __ballot_sync(kFull, !L.act);
       }
     }
@@ -1025,7 +1040,7 @@ int launch_select(const Params& p, uint32_t sel_grid, int shape, cudaStream_t s)
 template <int CMP>
 int launch_fused(const Params& p, uint32_t sel_grid, int shape, cudaStream_t s) {
   const int nw = kSelShapes[shape];
-  const size_t smem = sizeof(uint32_t) * p.nslots;
+  const size_t smem = 2 * sizeof(uint32_t) * p.nslots;  // chunk counts and maxima
   if (nw == 32) k_batched_select<float, CMP, 32, true><<<sel_grid, 32 * 32, smem, s>>>(p);
   else if (nw == 8) k_batched_select<float, CMP, 8, true><<<sel_grid, 8 * 32, smem, s>>>(p);
   else k_batched_select<float, CMP, 16, true><<<sel_grid, 16 * 32, smem, s>>>(p);
@@ -1190,7 +1205,6 @@ int set_schedule(ar_plan& pl, int shape, int gshare_pm) {
     set_cuda_error(e);
     return AR_ERR_CUDA;
   }
-  // the counters live in dynamic shared memory beside the kernel's own 8 KB:
   // beyond kMaxFusedSlots home realizations per CTA the call takes two launches
   pl.fused = fused && nslots > 0 && nslots <= kMaxFusedSlots;
   pl.nslots = nslots;

@@ -136,3 +136,24 @@ def test_fused_falls_back_for_very_long_home_lists(gb, orc):
     oo = np.arange(B + 1, dtype=np.int64)   # one selection per realization
     alpha = rng.exponential(1.0, size=int(off[-1])).astype(np.float32)
     _check(gb, orc, W.Batch(alpha, off, oo), 32)
+
+
+def test_unaligned_fp32_takes_two_launches(gb, orc):
+    """FP32 propensities whose base is not 16-byte aligned (a view one element
+    into a buffer): the one-launch form needs 16-byte loads, so the call takes
+    the two-launch form with the plan and gives the oracle's results."""
+    import torch
+    bt = W.batched_uneven(B=300, seed=311, K=64)
+    buf = torch.zeros(bt.alpha.size + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = torch.from_numpy(bt.alpha).cuda()
+    a = buf[1:]                                    # 4-byte aligned, not 16
+    assert a.data_ptr() % 16 != 0
+    plan = gb.Plan(bt.offsets, bt.out_offsets)
+    gb.ar_plan_set_tile(plan, 32, 0)
+    bs, idx, stats, st = gb.select_batched(a, _t(bt.offsets), _t(bt.out_offsets), plan=plan)
+    obs, oidx, ostats, ost = orc.select_batched(bt, nthreads=8)
+    np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
+    np.testing.assert_array_equal(stats.cpu().numpy().astype(np.uint64), ostats)
+    np.testing.assert_array_equal(bs.cpu().numpy()[:, 0], obs[:, 0])
+    assert int(st.item()) == ost
+    plan.close()
