@@ -59,6 +59,8 @@ def lib():
         L.orc_bound.restype = u32
         L.orc_select_ar.argtypes = [vp, i32, i64, dbl, i64, u64, u64, u32, i32, u64, vp, vp, i32]
         L.orc_select_ar.restype = u32
+        L.orc_select_runs.argtypes = [vp, i32, i64, dbl, i64, u64, u64, u32, i32, u64, vp, vp]
+        L.orc_select_runs.restype = u32
         L.orc_select_batched.argtypes = [vp, i32, vp, vp, i64, u64, u64, u32, i32, u64,
                                          vp, vp, vp, i32]
         L.orc_select_batched.restype = u32
@@ -125,6 +127,20 @@ def select_ar(alpha, K, seed=1, sel_offset=0, realization=0, cmp=CMP_F64,
     st = lib().orc_select_ar(_ptr(a), _dtype_code(a), a.size, T, K, ctypes.c_uint64(seed),
                              ctypes.c_uint64(sel_offset), realization, cmp,
                              ctypes.c_uint64(trial_cap), _ptr(idx), _ptr(stats), nthreads)
+    return idx, stats, int(st)
+
+
+def select_runs(alpha, K, seed=1, sel_offset=0, realization=0, cmp=CMP_F64,
+                bound_value=None, trial_cap=1 << 20):
+    """Selections sel_offset .. sel_offset + K - 1 drawn from runs of 64 (the
+    batched entry points' stream) -> (idx int32[K], stats uint64[3], status)."""
+    a = np.ascontiguousarray(alpha)
+    T = bound(a)[0] if bound_value is None else float(bound_value)
+    idx = np.zeros(K, dtype=np.int32)
+    stats = np.zeros(3, dtype=np.uint64)
+    st = lib().orc_select_runs(_ptr(a), _dtype_code(a), a.size, T, K, ctypes.c_uint64(seed),
+                               ctypes.c_uint64(sel_offset), realization, cmp,
+                               ctypes.c_uint64(trial_cap), _ptr(idx), _ptr(stats))
     return idx, stats, int(st)
 
 

@@ -217,6 +217,101 @@ uint32_t orc_select_ar(const void *alpha, int dtype, int64_t M, double T,
     return status;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Runs: the classical AR loop (Section "A GPU acceptance-rejection         */
+/* algorithm": draw a uniform candidate j and a uniform u, accept when      */
+/* u T < alpha_j, otherwise draw again) applied to consecutive selections   */
+/* on one random sequence.  Selections are grouped in runs of 64            */
+/* consecutive selection numbers; run g of realization b draws its trials   */
+/* n = 0, 1, 2, ... in order, and its decision r (selection 64 g + r) is    */
+/* the first accepted trial after decision r - 1, or the sentinel M once    */
+/* trial_cap trials in a row were rejected (the next decision then starts   */
+/* at the following trial).                                                 */
+/* Trial n of run g: with G = floor(n / 64), h = floor(n / 32) mod 2 and    */
+/* i = n mod 32, Philox block q = 32 G + i of counter                       */
+/* (q mod 2^32, g, b, 256 floor(q / 2^32)); words 2h and 2h+1 are (w_a,     */
+/* w_b), candidate and comparison as above.                                 */
+/* ------------------------------------------------------------------------ */
+#define RUN_LEN 64u
+
+static void run_trial_words(uint64_t seed, uint32_t g, uint32_t b, uint64_t n,
+                            uint32_t *wa, uint32_t *wb)
+{
+    uint64_t q = 32u * (n / 64u) + n % 32u;
+    int h = (int)((n / 32u) % 2u);
+    uint32_t ctr[4] = {(uint32_t)q, g, b, (uint32_t)(q >> 32) << 8};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, seed, w);
+    *wa = w[2 * h];
+    *wb = w[2 * h + 1];
+}
+
+/* Decisions first .. last - 1 of run g into out[0 .. last - first); adds the
+ * trials those decisions consumed and counts the capped ones. */
+static void select_run(const void *alpha, int dtype, int64_t M, double T, int cmp,
+                       uint64_t seed, uint32_t g, uint32_t b, uint32_t first,
+                       uint32_t last, uint64_t trial_cap, int32_t *out,
+                       uint64_t *trials, uint64_t *capped)
+{
+    float Tf = (float)T;
+    uint64_t n = 0;      /* next trial of the run */
+    for (uint32_t r = 0; r < last; r++) {
+        int64_t sel = M;  /* decision r: the sentinel unless a trial accepts */
+        uint64_t t;
+        for (t = 0; t < trial_cap; t++, n++) {
+            uint32_t wa, wb;
+            run_trial_words(seed, g, b, n, &wa, &wb);
+            int64_t j = candidate(wa, M);
+            double a = alpha_at(alpha, dtype, j);
+            int ok = (cmp == 0) ? accept_f32(wb, Tf, (float)a) : accept_f64(wb, T, a);
+            if (ok) {
+                sel = j;
+                n++;
+                t++;
+                break;
+            }
+        }
+        if (r >= first) {
+            out[r - first] = (int32_t)sel;
+            *trials += t;
+            if (sel == M) (*capped)++;
+        }
+    }
+}
+
+/* K selections from one propensity vector, numbers sel_offset + i, drawn
+ * from the runs that hold them.  stats = {trials, accepted, capped}. */
+uint32_t orc_select_runs(const void *alpha, int dtype, int64_t M, double T,
+                         int64_t K, uint64_t seed, uint64_t sel_offset,
+                         uint32_t realization, int cmp, uint64_t trial_cap,
+                         int32_t *idx, uint64_t stats[3])
+{
+    uint32_t status = bound_check(T, cmp);
+    if (status || T == 0.0 || M == 0) {
+        for (int64_t i = 0; i < K; i++) idx[i] = (int32_t)M;
+        if (!status && K > 0) status = ST_ALL_ZERO;
+        return status;
+    }
+    uint64_t trials = 0, capped = 0;
+    int64_t i = 0;
+    while (i < K) {
+        uint64_t s = sel_offset + (uint64_t)i;
+        uint32_t g = (uint32_t)(s / RUN_LEN), first = (uint32_t)(s % RUN_LEN);
+        uint32_t last = RUN_LEN;
+        if ((int64_t)(last - first) > K - i) last = first + (uint32_t)(K - i);
+        select_run(alpha, dtype, M, T, cmp, seed, g, realization, first, last, trial_cap,
+                   idx + i, &trials, &capped);
+        i += last - first;
+    }
+    if (capped) status |= ST_TRIAL_CAP;
+    if (stats) {
+        stats[0] += trials;
+        stats[1] += (uint64_t)K - capped;
+        stats[2] += capped;
+    }
+    return status;
+}
+
 /* Batched form: realization b owns alpha[offsets[b] .. offsets[b+1]) and
  * writes K_b = out_offsets[b+1] - out_offsets[b] indices at out_offsets[b].
  * Its bound is its own maximum (orc_bound); bound_sum[2b..2b+1] = (max, sum).
@@ -228,13 +323,20 @@ uint32_t orc_select_batched(const void *alpha, int dtype, const int64_t *offsets
                             uint64_t stats[3], int nthreads)
 {
     uint32_t status = 0;
-    uint64_t st[3] = {0, 0, 0};
+    uint64_t s0 = 0, s1 = 0, s2 = 0;
     int64_t esize = dtype == 0 ? 4 : 8;
+    (void)nthreads;
+    /* realizations are independent: one at a time per thread */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nthreads > 0 ? nthreads : 1) \
+    reduction(| : status) reduction(+ : s0, s1, s2)
+#endif
     for (int64_t b = 0; b < B; b++) {
         const char *ab = (const char *)alpha + offsets[b] * esize;
         int64_t Mb = offsets[b + 1] - offsets[b];
         int64_t Kb = out_offsets[b + 1] - out_offsets[b];
         double bs[2];
+        uint64_t st[3] = {0, 0, 0};
         uint32_t sb = orc_bound(ab, dtype, Mb, bs);
         if (sb & ST_BAD_ALPHA) {
             /* an invalid realization has no usable bound: (NaN, NaN), no
@@ -246,21 +348,25 @@ uint32_t orc_select_batched(const void *alpha, int dtype, const int64_t *offsets
         }
         bound_sum[2 * b] = bs[0];
         bound_sum[2 * b + 1] = bs[1];
-        status |= orc_select_ar(ab, dtype, Mb, bs[0], Kb, seed, sel_offset,
-                                realization_base + (uint32_t)b, cmp, trial_cap,
-                                idx + out_offsets[b], st, nthreads);
+        status |= orc_select_runs(ab, dtype, Mb, bs[0], Kb, seed, sel_offset,
+                                  realization_base + (uint32_t)b, cmp, trial_cap,
+                                  idx + out_offsets[b], st);
+        s0 += st[0];
+        s1 += st[1];
+        s2 += st[2];
     }
     if (stats) {
-        stats[0] += st[0];
-        stats[1] += st[1];
-        stats[2] += st[2];
+        stats[0] += s0;
+        stats[1] += s1;
+        stats[2] += s2;
     }
     return status;
 }
 
 /* Batched selection with the caller's bounds: realization b uses
  * T_b = bound[b * stride] (T_w = w * max_j alpha_j, the paper's threshold
- * experiment, keeps the law for w >= 1).  Each realization as orc_select_ar. */
+ * experiment, keeps the law for w >= 1).  Each realization as
+ * orc_select_runs. */
 uint32_t orc_select_batched_bounded(const void *alpha, int dtype, const int64_t *offsets,
                                     const int64_t *out_offsets, int64_t B, const double *bound,
                                     int64_t stride, uint64_t seed, uint64_t sel_offset,
@@ -268,13 +374,28 @@ uint32_t orc_select_batched_bounded(const void *alpha, int dtype, const int64_t 
                                     int32_t *idx, uint64_t stats[3], int nthreads)
 {
     uint32_t status = 0;
+    uint64_t s0 = 0, s1 = 0, s2 = 0;
     int64_t esize = dtype == 0 ? 4 : 8;
+    (void)nthreads;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nthreads > 0 ? nthreads : 1) \
+    reduction(| : status) reduction(+ : s0, s1, s2)
+#endif
     for (int64_t b = 0; b < B; b++) {
         const char *ab = (const char *)alpha + offsets[b] * esize;
-        status |= orc_select_ar(ab, dtype, offsets[b + 1] - offsets[b], bound[b * stride],
-                                out_offsets[b + 1] - out_offsets[b], seed, sel_offset,
-                                realization_base + (uint32_t)b, cmp, trial_cap,
-                                idx + out_offsets[b], stats, nthreads);
+        uint64_t st[3] = {0, 0, 0};
+        status |= orc_select_runs(ab, dtype, offsets[b + 1] - offsets[b], bound[b * stride],
+                                  out_offsets[b + 1] - out_offsets[b], seed, sel_offset,
+                                  realization_base + (uint32_t)b, cmp, trial_cap,
+                                  idx + out_offsets[b], st);
+        s0 += st[0];
+        s1 += st[1];
+        s2 += st[2];
+    }
+    if (stats) {
+        stats[0] += s0;
+        stats[1] += s1;
+        stats[2] += s2;
     }
     return status;
 }

@@ -266,7 +266,7 @@ def test_batched_oracle_matches_single(orc):
         a = bt.alpha[bt.offsets[b]:bt.offsets[b + 1]]
         mx, sm, _ = orc.bound(a)
         assert bs[b, 0] == mx and bs[b, 1] == sm
-        ib, _, _ = orc.select_ar(a, 40, seed=2, sel_offset=7, realization=10 + b, cmp=0)
+        ib, _, _ = orc.select_runs(a, 40, seed=2, sel_offset=7, realization=10 + b, cmp=0)
         np.testing.assert_array_equal(idx[bt.out_offsets[b]:bt.out_offsets[b + 1]], ib)
     assert int(stats[1]) == 6 * 40
 
