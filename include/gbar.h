@@ -40,6 +40,21 @@
  * alpha_j (Section "Election step"; experiments' T_w = w max alpha, w = 1).
  * Conditioned on acceptance the law is alpha_j / sum(alpha) up to the
  * 2^-32 candidate lattice and the 2^-24 / 2^-32 uniform lattice.
+ *
+ * Runs (the batched entry points ar_select_batched and
+ * ar_select_batched_bounded): selection ids are grouped in runs of 64,
+ * run g = floor(s / 64) holding selections 64 g .. 64 g + 63, and each run
+ * is one sequence of trials n = 0, 1, 2, ...: with G = floor(n / 64),
+ * h = floor(n / 32) mod 2, i = n mod 32, trial n reads words 2h and 2h+1 of
+ * the Philox block q = 32 G + i of counter
+ * (q mod 2^32, g, b, 256 floor(q / 2^32)), with j and the test as above.
+ * Selection 64 g + r is the first accepted trial after the one that decided
+ * selection 64 g + r - 1 (the classical AR loop run over consecutive
+ * selections), or M (AR_STATUS_TRIAL_CAP) after trial_cap consecutive
+ * rejected trials; the next selection then starts at the following trial.
+ * A selection's trials are those from the trial after the previous
+ * decision to its own.  Results do not depend on how the selections of a
+ * run are split over calls (sel_offset).
  */
 #ifndef GBAR_H
 #define GBAR_H
@@ -184,7 +199,7 @@ int ar_select_k(const void *d_alpha, int dtype, int64_t M, const double *d_bound
  * K_b = out_offsets[b+1] - out_offsets[b] indices at d_idx[out_offsets[b]].
  * Its bound is its own maximum, computed in the kernel; its Philox
  * realization id is realization_base + b; its selection ids are
- * sel_offset + 0 .. K_b-1.
+ * sel_offset + 0 .. K_b-1, drawn from runs of 64 (the random stream, top).
  *   d_alpha_cat      FP32 or FP64 (dtype).
  *   d_offsets        [B+1] int64, non-decreasing, offsets[0] = 0.
  *   d_out_offsets    [B+1] int64, non-decreasing, out_offsets[0] = 0.

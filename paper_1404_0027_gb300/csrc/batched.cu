@@ -67,7 +67,6 @@ constexpr uint32_t kChunk = 1024;  // reduction chunk (elements)
 constexpr int kVPL = kChunk / 32;  // elements per lane (register path)
 constexpr uint32_t kSItem = 64;     // selections per home work item
 constexpr uint32_t kGItem = 64;     // selections per global-queue work item
-constexpr int kU = 3;               // Philox blocks per lane per round
 
 // ---- plan-built work items -------------------------------------------------
 struct RItem {  // one reduction chunk: alpha_cat[e0, e0 + n)
@@ -118,8 +117,6 @@ struct Params {
   ar_stats* stats;
   uint32_t* status;
   unsigned long long cap;  // trials per selection, 1 .. 2^32
-  uint32_t capb;           // ceil(cap / 2): Philox blocks per selection
-  uint32_t cap_m1;         // cap - 1
   uint32_t B;
   uint32_t sel_base;
   uint32_t b_base;
@@ -479,6 +476,23 @@ __global__ void __launch_bounds__(kBNT) k_batched_bound(const Params p) {
 // fit in 128 bits; bits below 2^-96 of the maximum are dropped -- added
 // exactly and rounded once; FP64 data: FP64 sums in chunk order), stored by
 // lane 0 as {T, sum} ({NaN, NaN} when invalid), and the status bits.
+// The exact total of a realization's FP32 chunk partials (all valid), emax
+// above every chunk exponent, rounded once; the value is returned in lane 0.
+// Kept out of line: the selection loops that reach it stay small.
+__device__ __noinline__ double fold_sum_f32(const Part* __restrict__ parts, uint32_t nch, int emax) {
+  const uint32_t lane = threadIdx.x & 31u;
+  U128 acc;
+  for (uint32_t k = lane; k < nch; k += 32) {
+    const Part& q = parts[k];
+    U128 y;
+    y.hi = q.hi;
+    y.lo = q.lo;
+    acc = add128(acc, shr128(y, emax - q.e));
+  }
+  acc = warp_sum128(acc);
+  return lane == 0 ? u128_to_double(acc, emax) : 0.0;
+}
+
 template <typename TS>
 __device__ __forceinline__ void realization_bound(const Params& p, uint32_t p0, uint32_t nch,
                                                   uint32_t b, bool write, unsigned long long& vm,
@@ -510,17 +524,7 @@ __device__ __forceinline__ void realization_bound(const Params& p, uint32_t p0, 
   double sum = 0.0;
   if (!bd) {
     if constexpr (sizeof(TS) == 4) {
-      emax = __reduce_max_sync(kFull, emax) + 1;
-      U128 acc;
-      for (uint32_t k = lane; k < nch; k += 32) {
-        const Part& q = p.parts[p0 + k];
-        U128 y;
-        y.hi = q.hi;
-        y.lo = q.lo;
-        acc = add128(acc, shr128(y, emax - q.e));
-      }
-      acc = warp_sum128(acc);
-      if (lane == 0) sum = u128_to_double(acc, emax);
+      sum = fold_sum_f32(p.parts + p0, nch, __reduce_max_sync(kFull, emax) + 1);
     } else {
       if (lane == 0)
         for (uint32_t k = 0; k < nch; ++k)
@@ -570,15 +574,6 @@ template <int CMP>
 using BoundT = std::conditional_t<CMP == AR_CMP_F32, float, double>;
 
 template <typename TS, int CMP>
-struct Lane {
-  bool act = false;
-  uint32_t sel = 0, cnt = 0, M = 0, b = 0;
-  const TS* a = nullptr;
-  int32_t* out = nullptr;
-  BoundT<CMP> T = 0;
-};
-
-template <typename TS, int CMP>
 struct WItem {  // the warp's current item (identical in every lane)
   uint32_t b = 0, s = 0, s1 = 0, M = 0;
   const TS* a = nullptr;
@@ -597,46 +592,206 @@ __device__ __forceinline__ auto load_alpha(const TS* a, uint32_t j) {
   }
 }
 
-// Evaluates Philox blocks cnt .. cnt + kU - 1 of selection (sel, b): returns
-// the lowest accepted trial offset (0 .. 2kU - 1, or -1) and its candidate.
-// All gathers are issued before any test.  The trial cap is applied by the
-// caller (capped_hit): if the lowest accepted trial lies past the cap, no
-// trial below the cap was accepted.
-template <typename TS, int CMP>
-__device__ __forceinline__ int eval_blocks(const Params& p, uint32_t cnt, uint32_t sel, uint32_t b,
-                                           uint32_t M, const TS* a, BoundT<CMP> T, uint32_t& jh) {
-  uint4 w[kU];
+// Selections are made in runs of kRun consecutive selection numbers.  Run g
+// of realization b draws its trials n = 0, 1, 2, ... in order; trial
+// n = 64 G + 32 h + i (h in {0, 1}, i < 32) takes words 2h and 2h + 1 of
+// Philox block q = 32 G + i, counter (q mod 2^32, g, b, 256 floor(q / 2^32)).
+// Decision r of the run is selection g kRun + r: the first accepted trial
+// after decision r - 1 (the classical sequential AR loop), or the sentinel M
+// once trial_cap trials in a row were rejected.
+constexpr uint32_t kRun = 64;
+constexpr uint32_t kUMax = 3;  // Philox blocks per lane per warp round, at most
+
+// One warp round of U groups: lane l evaluates blocks 32 (G0 + u) + l
+// (u < U), i.e. trials 64 (G0 + u) + 32 h + l; acc[2u + h] and j[2u + h] are
+// that trial's test and candidate, A[u] / Bm[u] the warp's ballots of the
+// h = 0 / h = 1 trials of group u.
+template <typename TS, int CMP, int U, bool WIDE>
+__device__ __forceinline__ void round_eval(const Params& p, unsigned long long q0, uint32_t g,
+                                           uint32_t b, const WItem<TS, CMP>& w,
+                                           uint32_t (&j)[2 * U], bool (&acc)[2 * U],
+                                           uint32_t (&A)[U], uint32_t (&Bm)[U]) {
+  uint4 v[U];
 #pragma unroll
-  for (int u = 0; u < kU; ++u)
-    w[u] = philox10k(make_uint4(cnt + u, p.sel_base + sel, p.b_base + b, 0u), p.keys);
-  uint32_t j[2 * kU];
-#pragma unroll
-  for (int u = 0; u < kU; ++u) {
-    j[2 * u] = candidate(w[u].x, M);
-    j[2 * u + 1] = candidate(w[u].z, M);
+  for (int u = 0; u < U; ++u) {
+    const unsigned long long q = q0 + 32u * (uint32_t)u;
+    const uint32_t hi = WIDE ? (uint32_t)(q >> 32) << 8 : (uint32_t)(q0 >> 32) << 8;
+    v[u] = philox10k(make_uint4((uint32_t)q, g, b, hi), p.keys);
   }
-  decltype(load_alpha<TS, CMP>(a, 0u)) x[2 * kU];
 #pragma unroll
-  for (int t = 0; t < 2 * kU; ++t) x[t] = load_alpha<TS, CMP>(a, j[t]);
-  int hit = -1;
-#pragma unroll
-  for (int t = 2 * kU - 1; t >= 0; --t) {
-    const uint32_t wu = (t & 1) ? w[t >> 1].w : w[t >> 1].y;
-    bool acc;
-    if constexpr (CMP == AR_CMP_F32) acc = accept_f32(wu, T, x[t]);
-    else acc = accept_f64(wu, T, x[t]);
-    if (acc) {
-      hit = t;
-      jh = j[t];
-    }
+  for (int u = 0; u < U; ++u) {
+    j[2 * u] = candidate(v[u].x, w.M);
+    j[2 * u + 1] = candidate(v[u].z, w.M);
   }
-  return hit;
+  decltype(load_alpha<TS, CMP>(w.a, 0u)) x[2 * U];
+#pragma unroll
+  for (int t = 0; t < 2 * U; ++t) x[t] = load_alpha<TS, CMP>(w.a, j[t]);
+#pragma unroll
+  for (int t = 0; t < 2 * U; ++t) {
+    const uint32_t wu = (t & 1) ? v[t >> 1].w : v[t >> 1].y;
+    if constexpr (CMP == AR_CMP_F32) acc[t] = accept_f32(wu, w.T, x[t]);
+    else acc[t] = accept_f64(wu, w.T, x[t]);
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    A[u] = __ballot_sync(kFull, acc[2 * u]);
+    Bm[u] = __ballot_sync(kFull, acc[2 * u + 1]);
+  }
 }
 
-// The lowest accepted trial 2 cnt + hit counts only below the trial cap
-// (cap - 1 - 2 cnt >= 0 for an active selection, whose cnt < ceil(cap / 2)).
-__device__ __forceinline__ int capped_hit(const Params& p, uint32_t cnt, int hit) {
-  return (hit >= 0 && (uint32_t)hit > p.cap_m1 - 2u * cnt) ? -1 : hit;
+// Per-run state of a warp (identical in every lane).
+struct RunState {
+  uint32_t r;               // decisions made
+  uint32_t skip, rend;      // the item takes decisions [skip, rend)
+  uint32_t ncap;            // capped decisions in [skip, rend)
+  unsigned long long n;     // next trial (a multiple of 64)
+  unsigned long long since; // trials of decision r so far
+  unsigned long long t0;    // first trial of decision skip
+  bool done;
+};
+
+// A round in which no decision can reach the trial cap: decisions are the
+// accepted trials in order.  Candidates go to the warp's staging buffer at
+// their decision number (slot kRun for accepted trials past the run's end).
+template <typename TS, int CMP, int U>
+__device__ __forceinline__ void round_fast(const Params& p, uint32_t g, uint32_t b,
+                                           const WItem<TS, CMP>& w, RunState& rs,
+                                           int32_t* stage, SelCounters& cnt) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t lt = (1u << lane) - 1u;
+  uint32_t j[2 * U], A[U], Bm[U];
+  bool acc[2 * U];
+  round_eval<TS, CMP, U, false>(p, (rs.n >> 1) + lane, g, b, w, j, acc, A, Bm);
+  uint32_t c = rs.r, ra[2 * U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const uint32_t na = __popc(A[u]);
+    ra[2 * u] = c + __popc(A[u] & lt);
+    ra[2 * u + 1] = c + na + __popc(Bm[u] & lt);
+    c += na + __popc(Bm[u]);
+  }
+#pragma unroll
+  for (int t = 0; t < 2 * U; ++t)
+    stage[(acc[t] && ra[t] < rs.rend) ? ra[t] : kRun] = (int32_t)j[t];
+  if (c == rs.r) {
+    rs.since += 64u * U;
+    rs.n += 64u * U;
+    return;
+  }
+  // the trial offset in this round of decision `want` (one lane holds it)
+  auto offset_of = [&](uint32_t want) {
+    uint32_t o = 0xffffffffu;
+#pragma unroll
+    for (int t = 0; t < 2 * U; ++t)
+      if (acc[t] && ra[t] == want) o = 64u * (uint32_t)(t >> 1) + 32u * (uint32_t)(t & 1) + lane;
+    return __reduce_min_sync(kFull, o);
+  };
+  if (rs.r < rs.skip && c >= rs.skip) rs.t0 = rs.n + offset_of(rs.skip - 1u) + 1ull;
+  if (c >= rs.rend) {
+    const uint32_t o = offset_of(rs.rend - 1u);
+    if (lane == 0) cnt.trials += rs.n + o + 1ull - rs.t0;
+    rs.done = true;
+    return;
+  }
+  uint32_t last = 0;  // offset + 1 of the round's last acceptance
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (Bm[u]) last = 64u * (uint32_t)u + 32u + (32u - __clz(Bm[u]));
+    else if (A[u]) last = 64u * (uint32_t)u + (32u - __clz(A[u]));
+  }
+  rs.since = 64u * U - last;
+  rs.r = c;
+  rs.n += 64u * U;
+}
+
+// A round taken decision by decision, in trial order (a decision may reach
+// the trial cap, or the block index passes a multiple of 2^32).
+template <typename TS, int CMP>
+__device__ __forceinline__ void round_slow(const Params& p, uint32_t g, uint32_t b,
+                                           const WItem<TS, CMP>& w, RunState& rs,
+                                           int32_t* stage, SelCounters& cnt) {
+  constexpr int U = 1;
+  const uint32_t lane = threadIdx.x & 31u;
+  uint32_t j[2 * U], A[U], Bm[U];
+  bool acc[2 * U];
+  round_eval<TS, CMP, U, true>(p, (rs.n >> 1) + lane, g, b, w, j, acc, A, Bm);
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t m = h ? Bm[u] : A[u];
+#pragma unroll 1
+      for (uint32_t L = 0; L < 32u; ++L) {
+        const uint32_t jj = __shfl_sync(kFull, j[2 * u + h], L);
+        if (rs.done) continue;
+        const bool ok = ((m >> L) & 1u) != 0u;
+        ++rs.since;
+        if (!ok && rs.since != p.cap) continue;
+        if (rs.r >= rs.skip) {
+          if (lane == 0) stage[rs.r] = ok ? (int32_t)jj : (int32_t)w.M;
+          if (!ok) ++rs.ncap;
+        }
+        ++rs.r;
+        rs.since = 0;
+        const unsigned long long t = rs.n + 64u * (uint32_t)u + 32u * (uint32_t)h + L;
+        if (rs.r == rs.skip) rs.t0 = t + 1ull;
+        if (rs.r == rs.rend) {
+          rs.done = true;
+          if (lane == 0) cnt.trials += t + 1ull - rs.t0;
+        }
+      }
+    }
+  }
+  rs.n += 64u * U;
+}
+
+// Selections [w.s, w.s1) of the warp's item, run by run.  Each round takes
+// 1 .. kUMax blocks per lane, as many as the run's remaining decisions are
+// expected to need at the acceptance rate seen so far (the results do not
+// depend on the choice).
+template <typename TS, int CMP>
+__device__ __forceinline__ void run_item(const Params& p, const WItem<TS, CMP>& w,
+                                         int32_t* stage, SelCounters& cnt) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t bb = p.b_base + w.b;
+  uint32_t k = w.s;
+  while (k < w.s1) {
+    const uint32_t S = p.sel_base + k;
+    const uint32_t g = S / kRun;
+    RunState rs;
+    rs.skip = S % kRun;
+    rs.rend = min(kRun, rs.skip + (w.s1 - k));
+    rs.r = 0;
+    rs.ncap = 0;
+    rs.n = 0;
+    rs.since = 0;
+    rs.t0 = 0;
+    rs.done = false;
+    while (!rs.done) {
+      const unsigned long long qb = rs.n >> 1;
+      if (rs.since + 64u * kUMax < p.cap && (uint32_t)qb <= 0xffffffffu - 32u * kUMax) {
+        // expected trials of the remaining decisions: 8 each before the
+        // first acceptance, then n / r each
+        const unsigned long long left = rs.rend - rs.r;
+        const unsigned long long need = rs.r ? left * rs.n : left * 8u;
+        const unsigned long long per = rs.r ? (unsigned long long)rs.r : 1ull;
+        const uint32_t nu = need <= 64ull * per ? 1u : need <= 128ull * per ? 2u : 3u;
+        if (nu == 1u) round_fast<TS, CMP, 1>(p, g, bb, w, rs, stage, cnt);
+        else if (nu == 2u) round_fast<TS, CMP, 2>(p, g, bb, w, rs, stage, cnt);
+        else round_fast<TS, CMP, 3>(p, g, bb, w, rs, stage, cnt);
+      } else {
+        round_slow<TS, CMP>(p, g, bb, w, rs, stage, cnt);
+      }
+    }
+    __syncwarp();
+    for (uint32_t r = rs.skip + lane; r < rs.rend; r += 32u) w.out[k + (r - rs.skip)] = stage[r];
+    __syncwarp();
+    if (lane == 0) {
+      cnt.accepted += rs.rend - rs.skip - rs.ncap;
+      cnt.capped += rs.ncap;
+    }
+    k += rs.rend - rs.skip;
+  }
 }
 
 // Work claiming of one warp: the CTA's home list through a shared-memory
@@ -749,9 +904,14 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
         continue;
       }
     }
-    if (FUSED && s0 != 0) {
-      // fused, not the realization's first range: its maximum is in shared
-      // memory (the first range reduces the chunk partials: it writes the sum)
+    if (FUSED) {
+      // fused: the maximum is in shared memory; the realization's first range
+      // also combines the chunk partials into {T, sum} and the status
+      if (s0 == 0) {
+        unsigned long long vm;
+        uint32_t bd;
+        realization_bound<TS>(p, p0, nch, b, true, vm, bd, st_acc);
+      }
       const uint32_t tb = s_tmax[slot];
       if (tb == 0xffffffffu) st = 1;
       else if (tb == 0u || M == 0) st = AR_STATUS_ALL_ZERO;
@@ -816,12 +976,10 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
 template <typename TS, int CMP, int NW, bool FUSED = false>
 __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
     k_batched_select(const Params p) {
-  __shared__ uint32_t s_scr[NW * 64];
   __shared__ uint32_t s_queue;
+  __shared__ int32_t s_stage[NW * (kRun + 1)];  // per warp: the current run's decisions
   extern __shared__ uint32_t s_done[];  // fused: reduced chunks per home realization
   const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t lt = (1u << lane) - 1u;
-  uint32_t* scr = s_scr + (threadIdx.x >> 5) * 64;
   uint32_t q_end = 0;
   uint32_t nred = 0, r0 = 0;
   uint32_t* s_tmax = s_done + p.nslots;  // fused: maximum per home realization
@@ -860,132 +1018,10 @@ __global__ void __launch_bounds__(NW * 32, kSelThreadsPerSm / (NW * 32))
   }
   SelCounters cnt;
   uint32_t st_acc = 0;
-  Lane<TS, CMP> L;
   WItem<TS, CMP> cur;
   Claimer cl;
-  bool have = next_item<TS, CMP, FUSED>(p, &s_queue, q_end, cl, cur, st_acc, &pre, s_done, s_tmax);
-  bool tail = false;
-  for (;;) {
-    // ---- refill idle lanes from the current item (claiming the next one
-    // when it runs out); in the tail the remaining selections share lanes
-    if (!tail) {
-      uint32_t idle = __ballot_sync(kFull, !L.act);
-      while (idle && have) {
-        const uint32_t avail = cur.s1 - cur.s;
-        const uint32_t rank = __popc(idle & lt);
-        if (!L.act && rank < avail) {
-          L.act = true;
-          L.sel = cur.s + rank;
-          L.cnt = 0;
-          L.M = cur.M;
-          L.b = cur.b;
-          L.a = cur.a;
-          L.out = cur.out;
-          L.T = cur.T;
-        }
-        const uint32_t ni = __popc(idle);
-        cur.s += ni < avail ? ni : avail;
-        if (cur.s == cur.s1)
-          have = next_item<TS, CMP, FUSED>(p, &s_queue, q_end, cl, cur, st_acc, &pre, s_done,
-                                           s_tmax);
-        idle = __ballot_sync(kFull, !L.act);
-      }
-    }
-    const uint32_t act_mask = __ballot_sync(kFull, L.act);
-    if (!act_mask) break;
-    const uint32_t nA = __popc(act_mask);
-    if (!have && !tail && nA < 16) tail = true;
-    if (!tail) {
-      // ---- steady round: U Philox blocks of the lane's own selection
-      if (L.act) {
-        uint32_t jh = 0;
-        const int hit =
-            capped_hit(p, L.cnt, eval_blocks<TS, CMP>(p, L.cnt, L.sel, L.b, L.M, L.a, L.T, jh));
-        if (hit >= 0) {
-          L.out[L.sel] = (int32_t)jh;
-          cnt.trials += 2ull * L.cnt + (unsigned long long)hit + 1ull;
-          cnt.accepted += 1;
-          L.act = false;
-        } else {
-          L.cnt += kU;
-          if (L.cnt >= p.capb) {
-            L.out[L.sel] = (int32_t)L.M;
-            cnt.trials += p.cap;
-            cnt.capped += 1;
-            L.act = false;
-          }
-        }
-      }
-    } else {
-      // ---- tail round: compact the active selections into lanes [0, nA)
-      if (act_mask != (nA == 32 ? kFull : (1u << nA) - 1u)) {
-        if (L.act) scr[__popc(act_mask & lt)] = lane;
-        __syncwarp();
-        const uint32_t from = lane < nA ? scr[lane] : lane;
-        __syncwarp();
-        const uint32_t sel2 = __shfl_sync(kFull, L.sel, from);
-        const uint32_t cnt2 = __shfl_sync(kFull, L.cnt, from);
-        const uint32_t M2 = __shfl_sync(kFull, L.M, from);
-        const uint32_t b2 = __shfl_sync(kFull, L.b, from);
-        const TS* a2 =
-            reinterpret_cast<const TS*>(__shfl_sync(kFull, (unsigned long long)L.a, from));
-        int32_t* o2 =
-            reinterpret_cast<int32_t*>(__shfl_sync(kFull, (unsigned long long)L.out, from));
-        const BoundT<CMP> T2 = __shfl_sync(kFull, L.T, from);
-        L.act = lane < nA;
-        L.sel = sel2;
-        L.cnt = cnt2;
-        L.M = M2;
-        L.b = b2;
-        L.a = a2;
-        L.out = o2;
-        L.T = T2;
-      }
-      // G = 32 >> ceil(log2 nA) lanes per selection, U blocks per lane
-      const uint32_t lg = 5u - (32u - __clz(nA - 1u));
-      const uint32_t owner = lane >> lg;
-      const uint32_t g = lane & ((1u << lg) - 1u);
-      const bool valid = owner < nA;
-      const uint32_t src = owner & 31u;
-      const uint32_t o_sel = __shfl_sync(kFull, L.sel, src);
-      const uint32_t o_cnt = __shfl_sync(kFull, L.cnt, src) + g * kU;
-      const uint32_t o_M = __shfl_sync(kFull, L.M, src);
-      const uint32_t o_b = __shfl_sync(kFull, L.b, src);
-      const BoundT<CMP> o_T = __shfl_sync(kFull, L.T, src);
-      const TS* o_a =
-          reinterpret_cast<const TS*>(__shfl_sync(kFull, (unsigned long long)L.a, src));
-      int hit = -1;
-      uint32_t jh = 0;
-      if (valid && o_cnt < p.capb)
-        hit = capped_hit(p, o_cnt, eval_blocks<TS, CMP>(p, o_cnt, o_sel, o_b, o_M, o_a, o_T, jh));
-      const uint32_t bal = __ballot_sync(kFull, hit >= 0);
-      const uint32_t seg_lo = (lane << lg) & 31u;
-      const uint32_t seg_mask = lg == 5u ? kFull : ((1u << (1u << lg)) - 1u);
-      const uint32_t seg = (bal >> seg_lo) & seg_mask;
-      const uint32_t srcl = seg_lo + (uint32_t)(__ffs(seg) - 1);
-      const uint32_t got_j = __shfl_sync(kFull, jh, srcl & 31u);
-      const uint32_t got_h = (uint32_t)__shfl_sync(kFull, hit, srcl & 31u);
-      if (L.act) {
-        if (seg) {
-          // trial index 2(cnt + g U) + hit
-          const unsigned long long t_acc =
-              2ull * (L.cnt + (srcl - seg_lo) * kU) + (unsigned long long)got_h;
-          L.out[L.sel] = (int32_t)got_j;
-          cnt.trials += t_acc + 1ull;
-          cnt.accepted += 1;
-          L.act = false;
-        } else {
-          L.cnt += (1u << lg) * kU;
-          if (L.cnt >= p.capb) {
-            L.out[L.sel] = (int32_t)L.M;
-            cnt.trials += p.cap;
-            cnt.capped += 1;
-            L.act = false;
-          }
-        }
-      }
-    }
-  }
+  while (next_item<TS, CMP, FUSED>(p, &s_queue, q_end, cl, cur, st_acc, &pre, s_done, s_tmax))
+    run_item<TS, CMP>(p, cur, s_stage + (threadIdx.x >> 5) * (kRun + 1), cnt);
   if (cnt.capped) st_acc |= AR_STATUS_TRIAL_CAP;
   flush_counters(cnt, p.stats);
   st_acc = __reduce_or_sync(kFull, st_acc);
@@ -1384,8 +1420,6 @@ int selection_params(uint64_t seed, uint64_t sel_offset, uint32_t realization_ba
   p.idx = d_idx;
   p.stats = d_stats;
   p.cap = trial_cap;
-  p.capb = (uint32_t)((trial_cap + 1) / 2);
-  p.cap_m1 = (uint32_t)(trial_cap - 1);
   p.sel_base = (uint32_t)sel_offset;
   p.b_base = realization_base;
   p.keys = philox_keys(seed);
