@@ -82,21 +82,15 @@ struct SsaParams {
 
 // Mass-action propensity: one FP64 rounding of c times the exact count h.
 __device__ __forceinline__ double propensity(const SsaParams& p, int r, const int32_t* X) {
+  // every lane evaluates the same selects (no divergence over reaction types)
   const int type = __ldg(p.rtype + r);
   const int2 ab = __ldg(p.reac + r);
-  long long h;
-  if (type == 0) {
-    h = 1;
-  } else if (type == 1) {
-    const long long xa = X[ab.x];
-    h = xa > 0 ? xa : 0;
-  } else if (type == 2) {
-    const long long xa = X[ab.x], xb = X[ab.y];
-    h = (xa > 0 && xb > 0) ? xa * xb : 0;
-  } else {
-    const long long xa = X[ab.x];
-    h = xa >= 2 ? xa * (xa - 1) / 2 : 0;
-  }
+  const long long xa = type != 0 ? (long long)X[ab.x] : 0ll;
+  const long long xb = type == 2 ? (long long)X[ab.y] : 0ll;
+  long long h = 1;                                                    // 0: source
+  h = type == 1 ? (xa > 0 ? xa : 0ll) : h;                            // 1: A
+  h = type == 2 ? ((xa > 0 && xb > 0) ? xa * xb : 0ll) : h;           // 2: A + B
+  h = type == 3 ? (xa >= 2 ? (xa * (xa - 1)) >> 1 : 0ll) : h;         // 3: 2A
   return __dmul_rn(__ldg(p.rate + r), __ll2double_rn(h));
 }
 
