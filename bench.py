@@ -287,7 +287,7 @@ def run_reference(args, rank, world):
     dt = time.perf_counter() - t0
     value = acc / dt
     sample = (f"first {nb} of the {B_REAL} realizations of the batched workload per step "
-              f"({nb * K_B} selections, oracle C, FP32 comparison, OpenMP over selections)")
+              f"({nb * K_B} selections, oracle C, FP32 comparison, OpenMP over realizations)")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -318,7 +318,7 @@ def cpu_baseline_leg():
     return {"value": acc / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{reps} pass(es) over the full batched workload (slot 0: {B_REAL} "
                       f"realizations, {B_REAL * K_B} selections), oracle C, FP32 comparison, "
-                      f"OpenMP over selections, {dt:.1f} s"}
+                      f"OpenMP over realizations, {dt:.1f} s"}
 
 
 # --------------------------------------------------------------------------
