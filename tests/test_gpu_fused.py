@@ -157,3 +157,44 @@ def test_unaligned_fp32_takes_two_launches(gb, orc):
     np.testing.assert_array_equal(bs.cpu().numpy()[:, 0], obs[:, 0])
     assert int(st.item()) == ost
     plan.close()
+
+
+@pytest.mark.parametrize("use_plan", [False, True])
+def test_runs_split_over_calls(gb, orc, use_plan):
+    """One call drawing selections 0 .. 199 of every realization equals four
+    calls drawing 0 .. 36, 37 .. 74, 75 .. 127 and 128 .. 199 (runs of 64
+    split inside and at their boundaries): the same indices, and the trial
+    counters add up.  Both forms, with a plan (one launch) and without."""
+    K = 200
+    bt = W.batched_uneven(B=300, seed=312, K=K)
+    off = _t(bt.offsets)
+    a = _t(bt.alpha)
+
+    def call(lo, hi):
+        oo = np.arange(bt.B + 1, dtype=np.int64) * (hi - lo)
+        plan = None
+        if use_plan:
+            plan = gb.Plan(bt.offsets, oo)
+            gb.ar_plan_set_tile(plan, 32, 0)
+        bs, idx, stats, st = gb.select_batched(a, off, _t(oo), seed=9, sel_offset=lo,
+                                               realization_base=3, plan=plan)
+        out = idx.cpu().numpy().reshape(bt.B, hi - lo), stats.cpu().numpy(), int(st.item())
+        if plan is not None:
+            plan.close()
+        return out
+
+    full, sfull, st = call(0, K)
+    assert st == 0
+    parts, ssum = [], np.zeros(3, np.int64)
+    for lo, hi in ((0, 37), (37, 75), (75, 128), (128, K)):
+        idx, s, st = call(lo, hi)
+        assert st == 0
+        parts.append(idx)
+        ssum += s
+    np.testing.assert_array_equal(np.concatenate(parts, axis=1), full)
+    np.testing.assert_array_equal(ssum, sfull)
+    # and the oracle agrees with the single call
+    want_bs, want, _, _ = orc.select_batched(W.Batch(bt.alpha, bt.offsets,
+                                                     np.arange(bt.B + 1, dtype=np.int64) * K),
+                                             seed=9, realization_base=3, nthreads=8)
+    np.testing.assert_array_equal(full.ravel(), want)
