@@ -22,6 +22,7 @@ from __future__ import annotations
 import argparse
 import glob
 import hashlib
+import re
 import json
 import math
 import os
@@ -87,12 +88,23 @@ def measured_peaks():
         return 6800.0, "fallback", {}
 
 
+def _code_only(text: str) -> str:
+    """C/C++/CUDA source without comments and with whitespace collapsed, so
+    that the hash follows the code, not its documentation.  (Comment markers
+    inside string literals would be stripped too; the kernel sources have
+    none that matter.)"""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash() -> str:
+    """Hash of the kernel sources' code (comments and whitespace ignored)."""
     h = hashlib.sha256()
     for f in sorted(glob.glob(os.path.join(ROOT, "paper_1404_0027_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+        with open(f, encoding="utf-8") as fh:
             h.update(os.path.basename(f).encode())
-            h.update(fh.read())
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -27,7 +27,8 @@
 //       chunk maxima, the chunk sums aligned and added exactly in 128 bits and
 //       rounded once to FP64, the status.  In ar_select_batched the selection
 //       kernel does this instead when it claims a range of the realization
-//       (the bound), and for the realization's first range also the sum.
+//       (the bound; in the one-launch form the maximum comes from shared
+//       memory), and for the realization's first range also the sum.
 //   k_batched_select    the selections.  A plan gives each persistent CTA a
 //       home list of its realizations (the costliest ones, by
 //       longest-processing-time-first list scheduling) in ranges of 64
@@ -35,11 +36,12 @@
 //       warps of an SM work on a few realizations at a time and the
 //       gathers hit L1; the cheapest realizations form a global queue of
 //       64-selection ranges that the warps drain once their home list is
-//       empty.  A lane that finishes a selection takes the next one at once,
-//       so no warp waits for the slowest selection of a realization.  Per
-//       round a lane evaluates U Philox blocks (2U trials) of its own
-//       selection with all 2U gathers in flight at once; only when no work is
-//       left do the last selections share lanes.
+//       empty.  Selections come from runs of 64 (one trial sequence per run,
+//       its accepted trials in order are the run's selections): a warp takes
+//       one run at a time and evaluates 64, 128 or 192 consecutive trials of
+//       it per round (1-3 Philox blocks per lane, all gathers in flight at
+//       once); ballots and prefix counts number the accepted trials, and one
+//       coalesced copy per run writes them out.
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
