@@ -327,10 +327,23 @@ def cpu_baseline_leg():
         if time.perf_counter() - t0 > 10.0:
             break
     dt = time.perf_counter() - t0
+    # one host thread, about 3 s
+    t1 = time.perf_counter()
+    reps1 = acc1 = 0
+    while True:
+        _, _, st, _ = oracle.select_batched(bt, seed=SEED, nthreads=1)
+        acc1 += int(st[1])
+        reps1 += 1
+        if time.perf_counter() - t1 > 3.0:
+            break
+    dt1 = time.perf_counter() - t1
     return {"value": acc / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{reps} pass(es) over the full batched workload (slot 0: {B_REAL} "
                       f"realizations, {B_REAL * K_B} selections), oracle C, FP32 comparison, "
-                      f"OpenMP over realizations, {dt:.1f} s"}
+                      f"OpenMP over realizations, {dt:.1f} s",
+            "single_thread_value": acc1 / dt1,
+            "single_thread_sample": f"{reps1} pass(es) over the same workload on one host "
+                                    f"thread, {dt1:.1f} s"}
 
 
 # --------------------------------------------------------------------------
@@ -759,9 +772,29 @@ def main():
         f1.record(stream)
     torch.cuda.synchronize()
     plain_ms = f0.elapsed_time(f1) / npl
+    # the same pair captured 50 times in one graph: the device time per call
+    # without the host's cost of one graph launch per call
+    gp50 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gp50, stream=stream):
+        for _ in range(50):
+            plain()
+    for _ in range(3):
+        gp50.replay()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        f0.record(stream)
+        for _ in range(npl // 50):
+            gp50.replay()
+        f1.record(stream)
+    torch.cuda.synchronize()
+    plain_dev_ms = f0.elapsed_time(f1) / npl
     fp64_plain = {"value": 1000 / (plain_ms * 1e-3), "unit": UNIT, "ms_per_call": plain_ms,
+                  "device_ms_per_call": plain_dev_ms,
+                  "device_value": 1000 / (plain_dev_ms * 1e-3),
                   "workload": "one FP64 vector M=1024 alpha~U(0,1], K=1000 selections, "
-                              "ar_bound + ar_select_k, FP64 comparison, CUDA graph"}
+                              "ar_bound + ar_select_k, FP64 comparison, CUDA graph: one "
+                              "graph launch per call (value), 50 calls per graph launch "
+                              "(device_value)"}
 
     # ---- the single-vector workloads: skewed (M = 1029 lognormal with 30 %
     # zeros, K = 65536) and wide range (M = 2^20 spread over 12 decades,
@@ -841,6 +874,50 @@ def main():
                        workload="M=1029 FP32 lognormal(0,2), 309 zeros (seed 200), K=65536"),
         "wide_range": dict(single_leg(W.wide_range(1 << 20, seed=400), 1 << 20, 40),
                            workload="M=2^20 FP32 10^U(-6,6) (seed 400), K=2^20")}
+
+    # ---- the paper's timing workload: M = 1024 (Table 1's Gaussian
+    # propensities), 62 500 selections per launch, 10^7 in all; the paper's
+    # own election rule and the classical AR trial on the same data ---------
+    def paper_workload():
+        D = W.gaussian_paper(1024).astype(np.float32)
+        d_D = torch.from_numpy(D).to(dev)
+        T = torch.tensor([float(D.max())], dtype=torch.float64, device=dev)
+        Kp, calls = 62_500, 160
+        ix = torch.empty(Kp, dtype=torch.int32, device=dev)
+        rej = torch.zeros(1, dtype=torch.int64, device=dev)
+        stp = torch.zeros(1, dtype=torch.int32, device=dev)
+        out = {}
+        for name, fn in (
+                ("paper_rule", lambda c: gb.ar_select_paper(d_D, T, Kp, SEED, c * Kp, 0, ix, rej,
+                                                             stream)),
+                ("classical_ar", lambda c: gb.ar_select_k(d_D, T, Kp, SEED, c * Kp, 0,
+                                                          gb.AR_CMP_F32, 1 << 20, ix, None, stp,
+                                                          stream))):
+            with torch.cuda.stream(stream):
+                fn(0)
+            stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                for c in range(calls):
+                    fn(c)
+            g.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                g.replay()
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[name] = {"value": Kp * calls / (ms * 1e-3), "unit": UNIT, "ms_for_1e7": ms}
+        out["workload"] = ("M=1024 FP32 Gaussian (Table 1's propensities), 160 launches of "
+                           "62 500 selections = 10^7 selections in one CUDA graph")
+        out["paper_context"] = ("the paper's own rule took 2277.18 ms (Tesla M2075) and 1326.78 ms "
+                                "(Tesla K20) for this workload: context, not a target")
+        out["status"] = int(stp.item())
+        return out
+
+    paper_wl = paper_workload()
 
     # ---- full batched SSA: 10^4 realizations x 10^4 steps ------------------
     ssa = None
@@ -938,6 +1015,7 @@ def main():
            "cpu_baseline": cpu,
            "fp64_plain": fp64_plain,
            "single_vector": single,
+           "paper_workload": paper_wl,
            "ssa": ssa,
            "accuracy": {"batched_fp32_vs_fp64": acc_batched,
                         "skewed_fp32_vs_fp64": single["skewed"]["accuracy"],
