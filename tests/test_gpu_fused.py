@@ -198,3 +198,28 @@ def test_runs_split_over_calls(gb, orc, use_plan):
                                                      np.arange(bt.B + 1, dtype=np.int64) * K),
                                              seed=9, realization_base=3, nthreads=8)
     np.testing.assert_array_equal(full.ravel(), want)
+
+
+@pytest.mark.parametrize("cap", [300, 500, 1000])
+def test_cap_with_fast_and_stepwise_rounds(gb, orc, cap):
+    """Acceptance around 1 in 300 trials with caps of a few hundred trials:
+    runs mix 192-trial rounds with trial-by-trial rounds near the cap, and
+    many selections are capped.  Indices, trial counts and status equal the
+    oracle's on the bounded path (T_w = 60 max) and on the one-launch path
+    (one dominant propensity per realization)."""
+    bt = W.batched_uneven(B=120, seed=313, m_lo=64, m_hi=2000, K=64)
+    bw = 60.0 * np.array([bt.alpha[bt.offsets[b]:bt.offsets[b + 1]].max()
+                          for b in range(bt.B)], dtype=np.float64)
+    plan = gb.Plan(bt.offsets, bt.out_offsets)
+    idx, stats, st = gb.select_batched_bounded(_t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets),
+                                               _t(bw), 1, seed=4, trial_cap=cap, plan=plan)
+    oidx, ostats, ost = orc.select_batched_bounded(bt, bw, 1, seed=4, trial_cap=cap, nthreads=8)
+    np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
+    np.testing.assert_array_equal(stats.cpu().numpy().astype(np.uint64), ostats)
+    assert int(st.item()) == ost and ost & gb.AR_STATUS_TRIAL_CAP
+    assert 0 < ostats[2] < ostats[1]          # capped and accepted selections both occur
+    plan.close()
+    # one dominant propensity: M T / sum close to M
+    a = np.full(bt.alpha.size, 1e-3, dtype=np.float32)
+    a[bt.offsets[:-1]] = 1.0
+    _check(gb, orc, W.Batch(a, bt.offsets, bt.out_offsets), 16, seed=5, trial_cap=cap)
