@@ -9,10 +9,11 @@ else two) on the batched-uneven workload: B = 4096 realizations, M_b log-uniform
 comparison.  The launch is replayed from a captured CUDA graph.  Inputs are
 rotated over several independently drawn batches whose total size exceeds
 the 129 MB L2, so every step streams its propensities from HBM.  The
-headline throughput keeps two independent batches in flight (consecutive
-steps alternate between two streams, each batch with its own plan): one
-call's tail is filled by the other call's work.  The rate
-with one call at a time is reported beside it.
+headline throughput keeps several independent batches in flight
+(consecutive steps rotate over 2-4 streams, each batch with its own plan;
+the launch pattern -- tile, CTAs per SM, calls in flight -- is picked by
+timing): one call's tail and reduction overlap another call's selections.
+The rate with one call at a time is reported beside it.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
 the host cores instead (the comparison arm).
@@ -66,9 +67,8 @@ def workload_config():
                         "one ar_select_batched call per step from a CUDA graph (one kernel: "
                         "each CTA reduces then selects its own realizations), "
                         "selection tiles picked per batch by ar_plan_autotune; consecutive "
-                        "steps alternate between two streams (independent batches, one plan "
-                        "each), so two calls are in flight",
-            "batches_in_flight": 2,
+                        "steps rotate over several streams (independent batches, one plan "
+                        "each), so several calls are in flight (batches_in_flight)",
             "B": B_REAL, "K_b": K_B, "M_range": [M_LO, M_HI], "cmp": "f32", "seed": SEED,
             "l2": f"inputs rotated over {N_SLOTS} independently drawn batches "
                   f"(~{N_SLOTS * 52} MB > 129 MB L2)"}
@@ -455,7 +455,7 @@ def main():
 
     graphs = capture()
     K = args.steps
-    pipe = [stream, torch.cuda.Stream(dev)]  # the second stream of the pipelined run
+    pipe = [stream] + [torch.cuda.Stream(dev) for _ in range(3)]  # up to 4 calls in flight
 
     def replay(gs, nstreams, n, evs=None):
         """n steps, step i on stream i % nstreams after the events e[0]."""
@@ -534,39 +534,47 @@ def main():
     # one call at a time (per-step latency), with the autotuned tiles
     replay(graphs, 1, args.warmup)
     ms1, kern_ms, acc1, trials1, st1 = timed_run(graphs, 1, nvtx=True)
-    # two batches in flight: smaller CTAs share SMs with the other call's
-    # kernels better, so the tile is picked again for this launch pattern
+    # several batches in flight: the launch pattern is picked again by
+    # timing -- smaller CTAs, or fewer CTAs per SM (ar_plan_set_grid), let a
+    # call's kernel share the SMs with the other calls' kernels
     pipe_tiles = []
     best = None
     n_try = max(1, min(K, 600))
-    for cand in ("autotuned", (16, 0), (8, 300), (8, 0), (32, 0)):
+    for cand in (("autotuned", 0, 2), ((16, 0), 0, 2), ((8, 300), 0, 2), ((8, 0), 0, 2),
+                 ((32, 0), 0, 2), ((16, 0), 1, 3), ((16, 0), 1, 4)):
+        tile, grid, nst = cand
         for s, t in zip(slots, tuned):
-            gb.ar_plan_set_tile(s["plan"], *(t[:2] if cand == "autotuned" else cand))
-        us = rate_us(capture(), 2, n_try)
-        pipe_tiles.append({"tile": cand if cand == "autotuned" else list(cand),
-                           "us_per_step": us})
+            gb.ar_plan_set_tile(s["plan"], *(t[:2] if tile == "autotuned" else tile))
+            gb.ar_plan_set_grid(s["plan"], grid)
+        us = rate_us(capture(), nst, n_try)
+        pipe_tiles.append({"tile": tile if tile == "autotuned" else list(tile),
+                           "ctas_per_sm": grid if grid else "as many as fit",
+                           "in_flight": nst, "us_per_step": us})
         if best is None or us < best[1]:
             best = (cand, us)
+    best_tile, best_grid, in_flight = best[0]
     for s, t in zip(slots, tuned):
-        gb.ar_plan_set_tile(s["plan"], *(t[:2] if best[0] == "autotuned" else best[0]))
+        gb.ar_plan_set_tile(s["plan"], *(t[:2] if best_tile == "autotuned" else best_tile))
+        gb.ar_plan_set_grid(s["plan"], best_grid)
     # kernels the headline's K steps launch (step i replays slot i % N_SLOTS)
-    shares = [(t[1] if best[0] == "autotuned" else best[0][1]) for t in tuned]
+    shares = [(t[1] if best_tile == "autotuned" else best_tile[1]) for t in tuned]
     launches_timed = sum(launches_per_call(shares[i % N_SLOTS]) for i in range(K))
     graphs = capture()
-    replay(graphs, 2, args.warmup)
-    elapsed_ms, _, accepted, trials, status = timed_run(graphs, 2, nvtx=False)
+    replay(graphs, in_flight, args.warmup)
+    elapsed_ms, _, accepted, trials, status = timed_run(graphs, in_flight, nvtx=False)
     status |= st1
     t_wall1 = time.time()
     # the rest (kernels timed alone, end to end) runs one call at a time:
     # back to the autotuned tiles
     for s, t in zip(slots, tuned):
         gb.ar_plan_set_tile(s["plan"], *t[:2])
+        gb.ar_plan_set_grid(s["plan"], 0)
     time.sleep(0.2)
     sampler.stop()
     # every step selects B x K_b indices; the counters of the timed region
     # must say exactly that (no selection hits the trial cap on this data)
     sel_per_step = B_REAL * K_B
-    for name, acc in (("one call at a time", acc1), ("two in flight", accepted)):
+    for name, acc in (("one call at a time", acc1), ("several in flight", accepted)):
         if acc != K * sel_per_step:
             raise RuntimeError(f"{name}: {acc} accepted selections counted in the timed "
                                f"region, expected {K} steps x {sel_per_step}")
@@ -624,7 +632,7 @@ def main():
     sel_s = float(sel_ms.mean()) * 1e-3
     red_s = float(red_ms.mean()) * 1e-3
     alg_bytes = float(np.mean([algorithmic_bytes(s["bt"]) for s in slots]))
-    call_s = elapsed_ms / K * 1e-3               # per batch, two calls in flight
+    call_s = elapsed_ms / K * 1e-3               # per batch, several calls in flight
     step_s = float(kern_ms.mean()) * 1e-3        # per call, one call at a time
     # the headline: the whole call against the HBM roofline (algorithmic
     # bytes: alpha and the offsets read once, indices and {T, sum} written)
@@ -635,7 +643,8 @@ def main():
                 "traffic": profiled_traffic("ar_select_batched_call_batched_uneven.md"),
                 "kernel": "ar_select_batched (one launch of k_batched_select<float, AR_CMP_F32, "
                           "NW, fused> per call when the tile's global share is 0, else "
-                          "k_bound_reg + k_batched_select), two independent calls in flight",
+                          "k_bound_reg + k_batched_select), "
+                          f"{in_flight} independent calls in flight",
                 "algorithmic_bytes_per_launch": alg_bytes, "us_per_call": call_s * 1e6,
                 "one_call_at_a_time": {"achieved": alg_bytes / step_s / 1e9,
                                        "frac": alg_bytes / step_s / 1e9 / peak,
@@ -999,9 +1008,11 @@ def main():
            "config": dict(workload_config(),
                           autotuned_tiles=[{"warps_per_cta": t[0], "global_share_pm": t[1],
                                             "ns_per_call": t[2]} for t in tuned],
-                          tile_two_in_flight=(best[0] if best[0] == "autotuned"
-                                              else list(best[0])),
-                          two_in_flight_candidates=pipe_tiles),
+                          batches_in_flight=in_flight,
+                          tile_in_flight=(best_tile if best_tile == "autotuned"
+                                          else list(best_tile)),
+                          ctas_per_sm_in_flight=best_grid if best_grid else "as many as fit",
+                          in_flight_candidates=pipe_tiles),
            "clocks": clocks,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": e2e_ms / ke,

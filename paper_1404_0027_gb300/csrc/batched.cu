@@ -1099,6 +1099,7 @@ struct ar_plan {
   uint32_t nr, ns, grid, gq0;
   int shape;            // selection tile shape (index into kSelShapes)
   int gshare_pm;        // estimated cost left to the global queue, per mille
+  int ctas_per_sm = 0;  // 0: as many CTAs per SM as the tile's registers allow
   RItem* d_ritems;
   RInfo* d_rinfo;
   SItem* d_sitems;
@@ -1178,8 +1179,12 @@ void build_selection(const ar_plan& pl, uint32_t grid, double gshare, std::vecto
 // global-queue share (synchronous).
 int set_schedule(ar_plan& pl, int shape, int gshare_pm) {
   const DeviceInfo& dev = device_info();
-  const uint32_t grid = (uint32_t)std::max(1, dev.sm_count) *
-                        (uint32_t)(kSelThreadsPerSm / (kSelShapes[shape] * 32));
+  // CTAs per SM: as many as fit (at least 1 for every shape), or fewer when
+  // the caller runs several calls at once and wants them to share the SMs
+  const int fit = kSelThreadsPerSm / (kSelShapes[shape] * 32);
+  static_assert(kSelThreadsPerSm % (32 * 32) == 0, "every tile shape fits at least once per SM");
+  const int per_sm = pl.ctas_per_sm > 0 ? std::min(pl.ctas_per_sm, fit) : fit;
+  const uint32_t grid = (uint32_t)std::max(1, dev.sm_count) * (uint32_t)per_sm;
   std::vector<SItem> sitems;
   std::vector<uint32_t> scta;
   uint32_t gq0 = 0;
@@ -1529,6 +1534,18 @@ extern "C" int ar_plan_set_tile(ar_plan* plan, int warps_per_cta, int global_sha
   cudaGetDevice(&cur);
   if (cur != plan->device) return AR_ERR_ARG;
   return set_schedule(*plan, shape, global_share_pm);
+}
+
+extern "C" int ar_plan_set_grid(ar_plan* plan, int ctas_per_sm) {
+  if (!plan || ctas_per_sm < 0 || ctas_per_sm > kSelThreadsPerSm / (8 * 32)) return AR_ERR_ARG;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != plan->device) return AR_ERR_ARG;
+  const int old = plan->ctas_per_sm;
+  plan->ctas_per_sm = ctas_per_sm;
+  const int rc = set_schedule(*plan, plan->shape, plan->gshare_pm);
+  if (rc != AR_OK) plan->ctas_per_sm = old;
+  return rc;
 }
 
 extern "C" int ar_plan_autotune(ar_plan* plan, const void* d_alpha_cat, int dtype,
