@@ -541,7 +541,8 @@ def main():
     best = None
     n_try = max(1, min(K, 600))
     for cand in (("autotuned", 0, 2), ((16, 0), 0, 2), ((8, 300), 0, 2), ((8, 0), 0, 2),
-                 ((32, 0), 0, 2), ((16, 0), 1, 3), ((16, 0), 1, 4)):
+                 ((32, 0), 0, 2), ((16, 0), 1, 3), ((16, 0), 1, 4), ((8, 0), 2, 3),
+                 ((8, 0), 2, 4)):
         tile, grid, nst = cand
         for s, t in zip(slots, tuned):
             gb.ar_plan_set_tile(s["plan"], *(t[:2] if tile == "autotuned" else tile))
