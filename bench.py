@@ -540,23 +540,26 @@ def main():
     pipe_tiles = []
     best = None
     n_try = max(1, min(K, 600))
-    for cand in (("autotuned", 0, 2), ((16, 0), 0, 2), ((8, 300), 0, 2), ((8, 0), 0, 2),
-                 ((32, 0), 0, 2), ((16, 0), 1, 3), ((16, 0), 1, 4), ((8, 0), 2, 3),
-                 ((8, 0), 2, 4)):
-        tile, grid, nst = cand
+    # (tile, CTAs per SM, selections per item, calls in flight)
+    for cand in (("autotuned", 0, 0, 2), ((16, 0), 0, 0, 2), ((8, 300), 0, 0, 2),
+                 ((8, 0), 0, 0, 2), ((32, 0), 0, 0, 2), ((16, 0), 1, 0, 3), ((16, 0), 1, 0, 4),
+                 ((8, 0), 2, 0, 4), ((16, 0), 0, 256, 2), ((16, 0), 1, 128, 4),
+                 ((16, 0), 1, 256, 3), ((16, 0), 1, 256, 4)):
+        tile, grid, items, nst = cand
         for s, t in zip(slots, tuned):
             gb.ar_plan_set_tile(s["plan"], *(t[:2] if tile == "autotuned" else tile))
-            gb.ar_plan_set_grid(s["plan"], grid)
+            gb.ar_plan_set_grid(s["plan"], grid, items)
         us = rate_us(capture(), nst, n_try)
         pipe_tiles.append({"tile": tile if tile == "autotuned" else list(tile),
                            "ctas_per_sm": grid if grid else "as many as fit",
+                           "selections_per_item": items if items else 64,
                            "in_flight": nst, "us_per_step": us})
         if best is None or us < best[1]:
             best = (cand, us)
-    best_tile, best_grid, in_flight = best[0]
+    best_tile, best_grid, best_items, in_flight = best[0]
     for s, t in zip(slots, tuned):
         gb.ar_plan_set_tile(s["plan"], *(t[:2] if best_tile == "autotuned" else best_tile))
-        gb.ar_plan_set_grid(s["plan"], best_grid)
+        gb.ar_plan_set_grid(s["plan"], best_grid, best_items)
     # kernels the headline's K steps launch (step i replays slot i % N_SLOTS)
     shares = [(t[1] if best_tile == "autotuned" else best_tile[1]) for t in tuned]
     launches_timed = sum(launches_per_call(shares[i % N_SLOTS]) for i in range(K))
@@ -569,7 +572,7 @@ def main():
     # back to the autotuned tiles
     for s, t in zip(slots, tuned):
         gb.ar_plan_set_tile(s["plan"], *t[:2])
-        gb.ar_plan_set_grid(s["plan"], 0)
+        gb.ar_plan_set_grid(s["plan"], 0, 0)
     time.sleep(0.2)
     sampler.stop()
     # every step selects B x K_b indices; the counters of the timed region
@@ -1013,6 +1016,7 @@ def main():
                           tile_in_flight=(best_tile if best_tile == "autotuned"
                                           else list(best_tile)),
                           ctas_per_sm_in_flight=best_grid if best_grid else "as many as fit",
+                          selections_per_item_in_flight=best_items if best_items else 64,
                           in_flight_candidates=pipe_tiles),
            "clocks": clocks,
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

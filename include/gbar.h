@@ -333,20 +333,26 @@ int ar_plan_autotune(ar_plan *plan, const void *d_alpha_cat, int dtype,
 int ar_plan_set_tile(ar_plan *plan, int warps_per_cta, int global_share_pm);
 
 /* ---------------------------------------------------------------------
- * ar_plan_set_grid -- CTAs per SM that the plan's selection schedule is
- * built for: 0 (the default) = as many as the tile's register budget
- * allows (1, 2 or 4 for tiles of 32, 16 or 8 warps); 1..4 = at most that
- * many, so that a call's persistent CTAs occupy only part of each SM and
- * independent calls running at once on other streams (with plans of their
- * own) share the SMs -- one call's reduction then overlaps another's
- * selections.  Values above what the tile allows act as 0.  Rebuilds the
- * schedule for the current tile (synchronous; not capturable; no call with
- * this plan may be running; recapture CUDA graphs afterwards).  Results of
- * ar_select_batched do not depend on it.
- * Errors: AR_ERR_ARG for a NULL plan, a value outside 0..4 or another
+ * ar_plan_set_grid -- the persistent grid of the plan's selection
+ * schedule, for callers that keep several independent calls in flight on
+ * other streams (each with a plan of its own).
+ *   ctas_per_sm    0 (the default) = as many CTAs per SM as the tile's
+ *                  register budget allows (1, 2 or 4 for tiles of 32, 16 or
+ *                  8 warps); 1..4 = at most that many, so that a call's CTAs
+ *                  occupy only part of each SM and the calls in flight share
+ *                  the SMs -- one call's reduction then overlaps another's
+ *                  selections.  Values above what the tile allows act as 0.
+ *   selections_per_item  0 (the default, 64) or a multiple of 64 up to
+ *                  1024: the selection range a warp claims at a time in a
+ *                  CTA's home list.  Longer items mean fewer claims and
+ *                  bound lookups but a longer tail for one call alone.
+ * Rebuilds the schedule for the current tile (synchronous; not capturable;
+ * no call with this plan may be running; recapture CUDA graphs
+ * afterwards).  Results of ar_select_batched do not depend on either value.
+ * Errors: AR_ERR_ARG for a NULL plan, a value outside those sets or another
  * current device; AR_ERR_CUDA when the upload fails.
  * ------------------------------------------------------------------- */
-int ar_plan_set_grid(ar_plan *plan, int ctas_per_sm);
+int ar_plan_set_grid(ar_plan *plan, int ctas_per_sm, int selections_per_item);
 int ar_select_batched(const void *d_alpha_cat, int dtype, const int64_t *d_offsets,
                       const int64_t *d_out_offsets, int64_t B, uint64_t seed,
                       uint64_t sel_offset, uint32_t realization_base, int cmp,

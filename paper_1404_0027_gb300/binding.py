@@ -77,7 +77,7 @@ SIGNATURES = {
     "ar_select_batched_bounded": (_int, [_vp, _int, _vp, _vp, _i64, _vp, _i64, _u64, _u64, _u32,
                                          _int, _u64, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "ar_plan_set_tile": (_int, [_vp, _int, _int]),
-    "ar_plan_set_grid": (_int, [_vp, _int]),
+    "ar_plan_set_grid": (_int, [_vp, _int, _int]),
 }
 
 
@@ -319,9 +319,11 @@ def ar_plan_set_tile(plan, warps_per_cta, global_share_pm):
            "ar_plan_set_tile")
 
 
-def ar_plan_set_grid(plan, ctas_per_sm):
-    """CTAs per SM the plan's schedule is built for (0: as many as fit)."""
-    _check(lib().ar_plan_set_grid(_plan_ptr(plan), ctas_per_sm), "ar_plan_set_grid")
+def ar_plan_set_grid(plan, ctas_per_sm, selections_per_item=0):
+    """CTAs per SM (0: as many as fit) and selections per home work item
+    (0: 64) of the plan's schedule."""
+    _check(lib().ar_plan_set_grid(_plan_ptr(plan), ctas_per_sm, selections_per_item),
+           "ar_plan_set_grid")
 
 
 def ar_select_paper(D, bound, K, seed, sel_offset, realization, idx, rejections, stream=None):

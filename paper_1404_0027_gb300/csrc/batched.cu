@@ -67,7 +67,7 @@ constexpr int kBNT = kBWarps * 32;
 constexpr int kBCtasPerSm = 4;  // k_bound_reg: 32 warps per SM, 64 registers
 constexpr uint32_t kChunk = 1024;  // reduction chunk (elements)
 constexpr int kVPL = kChunk / 32;  // elements per lane (register path)
-constexpr uint32_t kSItem = 64;     // selections per home work item
+constexpr uint32_t kSItem = 64;     // selections per home work item (default)
 constexpr uint32_t kGItem = 64;     // selections per global-queue work item
 
 // ---- plan-built work items -------------------------------------------------
@@ -1100,6 +1100,7 @@ struct ar_plan {
   int shape;            // selection tile shape (index into kSelShapes)
   int gshare_pm;        // estimated cost left to the global queue, per mille
   int ctas_per_sm = 0;  // 0: as many CTAs per SM as the tile's registers allow
+  uint32_t item_sel = kSItem;  // selections per home work item
   RItem* d_ritems;
   RInfo* d_rinfo;
   SItem* d_sitems;
@@ -1168,7 +1169,7 @@ void build_selection(const ar_plan& pl, uint32_t grid, double gshare, std::vecto
   };
   scta.assign(grid + 1, 0);
   for (uint32_t c = 0; c < grid; ++c) {
-    for (int64_t b : lists[c]) add_items(b, kSItem);
+    for (int64_t b : lists[c]) add_items(b, pl.item_sel);
     scta[c + 1] = (uint32_t)sitems.size();
   }
   gq0 = (uint32_t)sitems.size();
@@ -1536,15 +1537,22 @@ extern "C" int ar_plan_set_tile(ar_plan* plan, int warps_per_cta, int global_sha
   return set_schedule(*plan, shape, global_share_pm);
 }
 
-extern "C" int ar_plan_set_grid(ar_plan* plan, int ctas_per_sm) {
+extern "C" int ar_plan_set_grid(ar_plan* plan, int ctas_per_sm, int selections_per_item) {
   if (!plan || ctas_per_sm < 0 || ctas_per_sm > kSelThreadsPerSm / (8 * 32)) return AR_ERR_ARG;
+  if (selections_per_item < 0 || selections_per_item > 1024 || selections_per_item % 64)
+    return AR_ERR_ARG;
   int cur = 0;
   cudaGetDevice(&cur);
   if (cur != plan->device) return AR_ERR_ARG;
   const int old = plan->ctas_per_sm;
+  const uint32_t old_item = plan->item_sel;
   plan->ctas_per_sm = ctas_per_sm;
+  plan->item_sel = selections_per_item ? (uint32_t)selections_per_item : kSItem;
   const int rc = set_schedule(*plan, plan->shape, plan->gshare_pm);
-  if (rc != AR_OK) plan->ctas_per_sm = old;
+  if (rc != AR_OK) {
+    plan->ctas_per_sm = old;
+    plan->item_sel = old_item;
+  }
   return rc;
 }
 

@@ -226,24 +226,26 @@ def test_cap_with_fast_and_stepwise_rounds(gb, orc, cap):
 
 
 def test_grid_setting(gb, orc):
-    """CTAs per SM 0 (as many as fit), 1, 2 and 4 with every tile: the same
-    indices, counters and status as the oracle; values outside 0..4 are
-    rejected and leave the plan usable."""
-    bt = W.batched_uneven(B=700, seed=314, K=96)
-    obs, oidx, ostats, ost = orc.select_batched(bt, seed=2, nthreads=8)
+    """CTAs per SM 0 (as many as fit), 1, 2 and 4 and items of 64, 128, 256 and
+    1024 selections with every tile: the same indices, counters and status
+    as the oracle (K_b = 300: items cut inside and across runs, sel_offset
+    not a multiple of 64); values outside the allowed sets are rejected and
+    leave the plan usable."""
+    bt = W.batched_uneven(B=700, seed=314, K=300)
+    obs, oidx, ostats, ost = orc.select_batched(bt, seed=2, sel_offset=37, nthreads=8)
     plan = gb.Plan(bt.offsets, bt.out_offsets)
     a, off, oo = _t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets)
     for warps in (8, 16, 32):
         gb.ar_plan_set_tile(plan, warps, 0)
-        for cps in (0, 1, 2, 4):
-            gb.ar_plan_set_grid(plan, cps)
-            bs, idx, stats, st = gb.select_batched(a, off, oo, seed=2, plan=plan)
+        for cps, items in ((0, 0), (1, 128), (2, 256), (4, 1024), (1, 64)):
+            gb.ar_plan_set_grid(plan, cps, items)
+            bs, idx, stats, st = gb.select_batched(a, off, oo, seed=2, sel_offset=37, plan=plan)
             np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
             np.testing.assert_array_equal(stats.cpu().numpy().astype(np.uint64), ostats)
             assert int(st.item()) == ost
-    for bad in (-1, 5):
+    for bad in ((-1, 0), (5, 0), (1, 32), (1, 2048), (0, -64)):
         with pytest.raises(gb.GbarError):
-            gb.ar_plan_set_grid(plan, bad)
-    bs, idx, _, _ = gb.select_batched(a, off, oo, seed=2, plan=plan)
+            gb.ar_plan_set_grid(plan, *bad)
+    bs, idx, _, _ = gb.select_batched(a, off, oo, seed=2, sel_offset=37, plan=plan)
     np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
     plan.close()

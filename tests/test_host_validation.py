@@ -158,8 +158,8 @@ def test_batched_selection_arguments(L, fn):
 
 def test_plan_set_tile_needs_a_plan(L):
     assert L.ar_plan_set_tile(None, 16, 0) == AR_ERR_ARG
-    assert L.ar_plan_set_grid(None, 1) == AR_ERR_ARG
-    assert L.ar_plan_set_grid(None, 0) == AR_ERR_ARG
+    assert L.ar_plan_set_grid(None, 1, 0) == AR_ERR_ARG
+    assert L.ar_plan_set_grid(None, 0, 128) == AR_ERR_ARG
 
 
 # ------------------------------------------------------------- comparators
