@@ -544,7 +544,7 @@ def main():
     for cand in (("autotuned", 0, 0, 2), ((16, 0), 0, 0, 2), ((8, 300), 0, 0, 2),
                  ((8, 0), 0, 0, 2), ((32, 0), 0, 0, 2), ((16, 0), 1, 0, 3), ((16, 0), 1, 0, 4),
                  ((8, 0), 2, 0, 4), ((16, 0), 0, 256, 2), ((16, 0), 1, 128, 4),
-                 ((16, 0), 1, 256, 3), ((16, 0), 1, 256, 4)):
+                 ((16, 0), 1, 256, 3), ((16, 0), 1, 256, 4), ((8, 0), 2, 256, 4)):
         tile, grid, items, nst = cand
         for s, t in zip(slots, tuned):
             gb.ar_plan_set_tile(s["plan"], *(t[:2] if tile == "autotuned" else tile))
