@@ -249,3 +249,32 @@ def test_grid_setting(gb, orc):
     bs, idx, _, _ = gb.select_batched(a, off, oo, seed=2, sel_offset=37, plan=plan)
     np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
     plan.close()
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("cmp", [0, 1])
+def test_grid_setting_two_launch_and_bounded(gb, orc, dtype, cmp):
+    """The plan's grid and item settings on the paths other than the
+    one-launch call: FP64 data (reduction, then selections), FP32 data with a
+    global queue, and ar_select_batched_bounded with the caller's bounds
+    T_w = 1.5 max.  Indices, counters and status equal the oracle's."""
+    bt = W.batched_uneven(B=500, seed=315, m_lo=16, m_hi=6000, K=200, dtype=dtype)
+    a, off, oo = _t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets)
+    plan = gb.Plan(bt.offsets, bt.out_offsets)
+    obs, oidx, ostats, ost = orc.select_batched(bt, seed=6, sel_offset=64, cmp=cmp, nthreads=8)
+    bw = 1.5 * obs[:, 0].copy()
+    bidx, bstats, bst = orc.select_batched_bounded(bt, bw, 1, seed=7, cmp=cmp, nthreads=8)
+    for tile, share, cps, items in ((16, 0, 1, 256), (8, 400, 2, 128), (32, 0, 0, 64)):
+        gb.ar_plan_set_tile(plan, tile, share)
+        gb.ar_plan_set_grid(plan, cps, items)
+        bs, idx, stats, st = gb.select_batched(a, off, oo, seed=6, sel_offset=64, cmp=cmp,
+                                               plan=plan)
+        np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
+        np.testing.assert_array_equal(stats.cpu().numpy().astype(np.uint64), ostats)
+        assert int(st.item()) == ost
+        idx2, stats2, st2 = gb.select_batched_bounded(a, off, oo, _t(bw), 1, seed=7, cmp=cmp,
+                                                      plan=plan)
+        np.testing.assert_array_equal(idx2.cpu().numpy(), bidx)
+        np.testing.assert_array_equal(stats2.cpu().numpy().astype(np.uint64), bstats)
+        assert int(st2.item()) == bst
+    plan.close()
