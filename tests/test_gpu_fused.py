@@ -278,3 +278,30 @@ def test_grid_setting_two_launch_and_bounded(gb, orc, dtype, cmp):
         np.testing.assert_array_equal(stats2.cpu().numpy().astype(np.uint64), bstats)
         assert int(st2.item()) == bst
     plan.close()
+
+
+@pytest.mark.parametrize("cps, items", [(1, 256), (2, 1024), (4, 64)])
+def test_grid_setting_tiny_and_ragged_batches(gb, orc, cps, items):
+    """Grid and item settings on batches far smaller than the grid (most CTAs
+    have empty home lists) and with empty realizations, realizations without
+    selections and K_b not a multiple of 64."""
+    cases = [
+        W.batch_from_vectors([W.skewed(50, seed=1).astype(np.float32)], [7]),
+        W.batch_from_vectors([W.skewed(m, seed=m).astype(np.float32) for m in (3, 700, 1)],
+                             [300, 0, 65]),
+        W.batch_from_vectors([np.zeros(0, np.float32), W.skewed(2000, seed=9).astype(np.float32),
+                              np.zeros(40, np.float32), W.skewed(10, seed=3).astype(np.float32)],
+                             [5, 1000, 3, 129]),
+    ]
+    for bt in cases:
+        obs, oidx, ostats, ost = orc.select_batched(bt, seed=8, sel_offset=5, nthreads=8)
+        plan = gb.Plan(bt.offsets, bt.out_offsets)
+        gb.ar_plan_set_tile(plan, 16, 0)
+        gb.ar_plan_set_grid(plan, cps, items)
+        bs, idx, stats, st = gb.select_batched(_t(bt.alpha), _t(bt.offsets), _t(bt.out_offsets),
+                                               seed=8, sel_offset=5, plan=plan)
+        np.testing.assert_array_equal(idx.cpu().numpy(), oidx)
+        np.testing.assert_array_equal(stats.cpu().numpy().astype(np.uint64), ostats)
+        np.testing.assert_array_equal(np.isnan(bs.cpu().numpy()), np.isnan(obs))
+        assert int(st.item()) == ost
+        plan.close()
