@@ -478,18 +478,21 @@ __global__ void __launch_bounds__(kBNT) k_batched_bound(const Params p) {
 // fit in 128 bits; bits below 2^-96 of the maximum are dropped -- added
 // exactly and rounded once; FP64 data: FP64 sums in chunk order), stored by
 // lane 0 as {T, sum} ({NaN, NaN} when invalid), and the status bits.
+// Chunk partials are read from L2 (ld.global.cg): in the one-launch form they
+// were written earlier in the same launch, so the read-only (non-coherent)
+// load path, whose data must not change during the launch, is not theirs.
 // The exact total of a realization's FP32 chunk partials (all valid), emax
 // above every chunk exponent, rounded once; the value is returned in lane 0.
 // Kept out of line: the selection loops that reach it stay small.
-__device__ __noinline__ double fold_sum_f32(const Part* __restrict__ parts, uint32_t nch, int emax) {
+__device__ __noinline__ double fold_sum_f32(const Part* parts, uint32_t nch, int emax) {
   const uint32_t lane = threadIdx.x & 31u;
   U128 acc;
   for (uint32_t k = lane; k < nch; k += 32) {
-    const Part& q = parts[k];
+    const Part* q = parts + k;
     U128 y;
-    y.hi = q.hi;
-    y.lo = q.lo;
-    acc = add128(acc, shr128(y, emax - q.e));
+    y.hi = __ldcg(&q->hi);
+    y.lo = __ldcg(&q->lo);
+    acc = add128(acc, shr128(y, emax - __ldcg(&q->e)));
   }
   acc = warp_sum128(acc);
   return lane == 0 ? u128_to_double(acc, emax) : 0.0;
@@ -506,18 +509,18 @@ __device__ __forceinline__ void realization_bound(const Params& p, uint32_t p0, 
   if constexpr (sizeof(TS) == 4) {
     uint32_t v32 = 0;
     for (uint32_t k = lane; k < nch; k += 32) {
-      const Part& q = p.parts[p0 + k];
-      v32 = max(v32, (uint32_t)q.vmax);
-      bd |= q.bad;
-      emax = max(emax, q.e);
+      const Part* q = p.parts + p0 + k;
+      v32 = max(v32, (uint32_t)__ldcg(&q->vmax));
+      bd |= __ldcg(&q->bad);
+      emax = max(emax, __ldcg(&q->e));
     }
     vm = __reduce_max_sync(kFull, v32);
   } else {
     for (uint32_t k = lane; k < nch; k += 32) {
-      const Part& q = p.parts[p0 + k];
-      const unsigned long long x = q.vmax;
+      const Part* q = p.parts + p0 + k;
+      const unsigned long long x = __ldcg(&q->vmax);
       vm = x > vm ? x : vm;
-      bd |= q.bad;
+      bd |= __ldcg(&q->bad);
     }
     vm = warp_max_u64(vm);
   }
@@ -530,7 +533,7 @@ __device__ __forceinline__ void realization_bound(const Params& p, uint32_t p0, 
     } else {
       if (lane == 0)
         for (uint32_t k = 0; k < nch; ++k)
-          sum = __dadd_rn(sum, __longlong_as_double((long long)p.parts[p0 + k].lo));
+          sum = __dadd_rn(sum, __longlong_as_double((long long)__ldcg(&p.parts[p0 + k].lo)));
     }
   }
   if (lane == 0) {

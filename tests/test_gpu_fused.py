@@ -305,3 +305,95 @@ def test_grid_setting_tiny_and_ragged_batches(gb, orc, cps, items):
         np.testing.assert_array_equal(np.isnan(bs.cpu().numpy()), np.isnan(obs))
         assert int(st.item()) == ost
         plan.close()
+
+
+def _bound_data(offsets, seed):
+    """FP32 Exp(1) propensities for the offsets; realization 4 all zero and a
+    NaN in realization 6 (BAD_ALPHA)."""
+    a = np.random.default_rng(seed).exponential(1.0, int(offsets[-1])).astype(np.float32)
+    a[offsets[4]:offsets[5]] = 0.0
+    a[offsets[6] + 500] = np.nan
+    return a
+
+
+def _bound_exact(a, offsets):
+    """{max, correctly rounded sum} per valid realization (NaN row otherwise)."""
+    import math
+    B = len(offsets) - 1
+    out = np.zeros((B, 2))
+    for b in range(B):
+        seg = a[offsets[b]:offsets[b + 1]]
+        if np.isnan(seg).any():
+            out[b] = np.nan
+        elif seg.size:
+            out[b] = float(seg.max()), math.fsum(seg.astype(np.float64))
+    return out
+
+
+@pytest.mark.parametrize("full", [False, True])
+def test_bound_batched_exact_paths_and_replays(gb, full):
+    """ar_bound_batched: exact maxima and correctly rounded FP32 totals, bit
+    for bit the same from the plan's vector path (16-byte aligned data), its
+    register path (the same data at an address that is not 16-byte aligned)
+    and the plan-less path, with the same status (ALL_ZERO, BAD_ALPHA).
+    Repeated calls on new data with the same plan, and replays of a captured
+    graph on new data in the same buffer, rewrite every output row."""
+    import torch
+    if full:   # the benchmark's batch shape: 4096 realizations, M_b in [64, 16384]
+        ms = np.diff(W.batched_uneven(B=4096, seed=300, m_lo=64, m_hi=16384, K=1).offsets)
+        ms[[4, 6]] = [1024, 3000]
+        ms[0] = 0
+    else:      # empty, single-element, one-chunk, chunk-edge, many-chunk realizations
+        ms = np.array([0, 1, 3, 17, 1024, 1025, 4099, 20_000, 70_000] +
+                      list(np.random.default_rng(7).integers(1, 5000, 200)))
+    offsets = np.concatenate([[0], np.cumsum(ms)]).astype(np.int64)
+    B = len(ms)
+    plan = gb.Plan(offsets, np.arange(B + 1, dtype=np.int64))
+    off_d = _t(offsets)
+    stream = torch.cuda.Stream()
+    want_st = gb.AR_STATUS_ALL_ZERO | gb.AR_STATUS_BAD_ALPHA
+
+    def run(alpha, pl):
+        bs = torch.full((B, 2), -7.0, dtype=torch.float64, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        gb.ar_bound_batched(alpha, off_d, pl, bs, st, None if pl is not None else
+                            torch.zeros(gb.ar_select_batched_workspace_size(B), dtype=torch.uint8,
+                                        device="cuda"), stream)
+        stream.synchronize()
+        return bs.cpu().numpy(), int(st.item())
+
+    for seed in (11, 12, 13):
+        a = _bound_data(offsets, seed)
+        alpha = _t(a)
+        assert alpha.data_ptr() % 16 == 0
+        got, st = run(alpha, plan)
+        buf = torch.empty(alpha.numel() + 1, dtype=torch.float32, device="cuda")
+        buf[1:].copy_(alpha)
+        two, st2 = run(buf[1:], plan)        # not 16-byte aligned: two launches
+        nop, st3 = run(alpha, None)
+        exact = _bound_exact(a, offsets)
+        np.testing.assert_array_equal(got, exact)
+        np.testing.assert_array_equal(got.view(np.int64), two.view(np.int64))
+        np.testing.assert_array_equal(got.view(np.int64), nop.view(np.int64))
+        assert st == st2 == st3 == want_st
+
+    # a captured call replayed on new data in the same buffer
+    alpha_g = torch.empty(int(offsets[-1]), dtype=torch.float32, device="cuda")
+    bs_g = torch.empty((B, 2), dtype=torch.float64, device="cuda")
+    st_g = torch.zeros(1, dtype=torch.int32, device="cuda")
+    alpha_g.copy_(_t(_bound_data(offsets, 20)))
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        gb.ar_bound_batched(alpha_g, off_d, plan, bs_g, st_g, None, stream)
+    for seed in (21, 22, 23):
+        a = _bound_data(offsets, seed)
+        alpha_g.copy_(_t(a))
+        bs_g.fill_(-7.0)
+        st_g.zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(bs_g.cpu().numpy(), _bound_exact(a, offsets))
+        assert int(st_g.item()) == want_st
+    plan.close()
