@@ -899,8 +899,8 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
         ++spins;
       }
       __syncwarp();
-      // pairs with the reducing warp's fence: its chunk partials, read below
-      // through this SM's L1 (the CTA's point of coherence), are visible
+      // pairs with the reducing warp's CTA-scope fence (both warps are in this
+      // CTA): its chunk partials, read below, are visible
       __threadfence_block();
       if (spins >= kFusedWaitLimit) {
         st_acc |= AR_STATUS_WAIT_LIMIT;
