@@ -816,7 +816,8 @@ def main():
         d_al = torch.from_numpy(alpha_np).to(dev)
         bs1 = torch.empty(2, dtype=torch.float64, device=dev)
         st1 = torch.zeros(1, dtype=torch.int32, device=dev)
-        wk = torch.zeros(max(gb.ar_bound_workspace_size(d_al.numel(), 0), 16),
+        dt = gb.AR_F64 if d_al.dtype == torch.float64 else gb.AR_F32
+        wk = torch.zeros(max(gb.ar_bound_workspace_size(d_al.numel(), dt), 16),
                          dtype=torch.uint8, device=dev)  # zero-filled before first use
         ix = torch.empty(K, dtype=torch.int32, device=dev)
         sts = torch.zeros(3, dtype=torch.int64, device=dev)
@@ -883,6 +884,9 @@ def main():
                 "accuracy": accuracy, "status": int(st1.item())}
 
     single = {
+        # the plain vector with the FP32 comparison (the FP64 one is fp64_plain)
+        "plain": dict(single_leg(W.plain_uniform(1024, seed=101), 1000, 2000),
+                      workload="M=1024 FP64 alpha~U(0,1] (seed 101), K=1000, FP32 comparison"),
         "skewed": dict(single_leg(W.skewed(1029, seed=200), 65536, 400),
                        workload="M=1029 FP32 lognormal(0,2), 309 zeros (seed 200), K=65536"),
         "wide_range": dict(single_leg(W.wide_range(1 << 20, seed=400), 1 << 20, 40),
@@ -1034,6 +1038,7 @@ def main():
            "paper_workload": paper_wl,
            "ssa": ssa,
            "accuracy": {"batched_fp32_vs_fp64": acc_batched,
+                        "plain_fp32_vs_fp64": single["plain"]["accuracy"],
                         "skewed_fp32_vs_fp64": single["skewed"]["accuracy"],
                         "wide_range_fp32_vs_fp64": single["wide_range"]["accuracy"],
                         "note": "FP64 indices of the library are bit-exact with the FP64 oracle "

@@ -2,8 +2,9 @@
 quality experiment draws 10^7 selections, Results, "Quality of the selection
 of the reaction indexes").
 
-For the skewed vector (M = 1029, lognormal, 309 zeros), the wide-range vector
-(M = 2^20 over 12 decades) and the batched workload, the FP32 and FP64
+For the plain vector (M = 1024 FP64 Uniform(0,1]), the skewed vector
+(M = 1029, lognormal, 309 zeros), the wide-range vector (M = 2^20 over 12
+decades) and the batched workload, the FP32 and FP64
 comparisons run on identical Philox streams.  Asserted:
 * the paired index-mismatch rate and the paired TV are <= 1e-3;
 * the FP32 histogram fits alpha_j / sum(alpha) (chi-square, bins merged to an
@@ -49,9 +50,11 @@ def _single(gb, alpha):
     return out[gb.AR_CMP_F32], out[gb.AR_CMP_F64]
 
 
-@pytest.mark.parametrize("name", ["skewed", "wide_range"])
+@pytest.mark.parametrize("name", ["plain", "skewed", "wide_range"])
 def test_fp32_accuracy_at_1e7(gb, orc, name):
-    alpha = W.skewed(1029, seed=200) if name == "skewed" else W.wide_range(1 << 20, seed=400)
+    alpha = {"plain": lambda: W.plain_uniform(1024, seed=101),
+             "skewed": lambda: W.skewed(1029, seed=200),
+             "wide_range": lambda: W.wide_range(1 << 20, seed=400)}[name]()
     i32, i64 = _single(gb, alpha)
     # the first selections of each precision are the oracle's
     for cmp, got in ((0, i32), (1, i64)):
