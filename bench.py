@@ -1033,7 +1033,11 @@ def main():
            "roofline_alu": roofline_alu,
            "roofline_reduction": roofline_reduction,
            "cpu_baseline": cpu,
-           "fp64_plain": fp64_plain,
+           # the metric's comparison: the FP32 batched rate over the plain FP64
+           # single-vector form's (one graph launch per call; device time)
+           "fp64_plain": dict(fp64_plain, fp32_batched_over_fp64_plain=value / fp64_plain["value"],
+                              fp32_batched_over_fp64_plain_device=value
+                              / fp64_plain["device_value"]),
            "single_vector": single,
            "paper_workload": paper_wl,
            "ssa": ssa,
