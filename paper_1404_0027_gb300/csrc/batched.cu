@@ -577,24 +577,29 @@ __global__ void __launch_bounds__(kBNT) k_batched_combine(const Params p) {
 // The bound in the comparison's precision.
 template <int CMP>
 using BoundT = std::conditional_t<CMP == AR_CMP_F32, float, double>;
+// The bound a warp's item carries: FP32, or FP64 with the FP32 pre-filter's
+// precomputation.
+template <int CMP>
+using ItemBound = std::conditional_t<CMP == AR_CMP_F32, float, F64Bound>;
+template <int CMP>
+__device__ __forceinline__ ItemBound<CMP> item_bound(BoundT<CMP> T) {
+  if constexpr (CMP == AR_CMP_F32) return T;
+  else return f64_bound(T);
+}
 
 template <typename TS, int CMP>
 struct WItem {  // the warp's current item (identical in every lane)
   uint32_t b = 0, s = 0, s1 = 0, M = 0;
   const TS* a = nullptr;
   int32_t* out = nullptr;
-  BoundT<CMP> T = 0;
+  ItemBound<CMP> T{};
 };
 
-// The comparison operand alpha_j: FP32 or FP64 per the comparison precision.
-template <typename TS, int CMP>
-__device__ __forceinline__ auto load_alpha(const TS* a, uint32_t j) {
-  if constexpr (CMP == AR_CMP_F32) {
-    if constexpr (sizeof(TS) == 4) return __ldg(a + j);
-    else return __double2float_rn(__ldg(a + j));
-  } else {
-    return (double)__ldg(a + j);
-  }
+// The FP32 comparison's operand alpha_j (FP64 data rounded to FP32).
+template <typename TS>
+__device__ __forceinline__ float load_alpha(const TS* a, uint32_t j) {
+  if constexpr (sizeof(TS) == 4) return __ldg(a + j);
+  else return __double2float_rn(__ldg(a + j));
 }
 
 // Selections are made in runs of kRun consecutive selection numbers.  Run g
@@ -628,14 +633,22 @@ __device__ __forceinline__ void round_eval(const Params& p, unsigned long long q
     j[2 * u] = candidate(v[u].x, w.M);
     j[2 * u + 1] = candidate(v[u].z, w.M);
   }
-  decltype(load_alpha<TS, CMP>(w.a, 0u)) x[2 * U];
+  if constexpr (CMP == AR_CMP_F32) {
+    float x[2 * U];
 #pragma unroll
-  for (int t = 0; t < 2 * U; ++t) x[t] = load_alpha<TS, CMP>(w.a, j[t]);
+    for (int t = 0; t < 2 * U; ++t) x[t] = load_alpha<TS>(w.a, j[t]);
 #pragma unroll
-  for (int t = 0; t < 2 * U; ++t) {
-    const uint32_t wu = (t & 1) ? v[t >> 1].w : v[t >> 1].y;
-    if constexpr (CMP == AR_CMP_F32) acc[t] = accept_f32(wu, w.T, x[t]);
-    else acc[t] = accept_f64(wu, w.T, x[t]);
+    for (int t = 0; t < 2 * U; ++t) {
+      const uint32_t wu = (t & 1) ? v[t >> 1].w : v[t >> 1].y;
+      acc[t] = accept_f32(wu, w.T, x[t]);
+    }
+  } else {
+    // the FP64 test, decided in FP32 where the margins allow it
+#pragma unroll
+    for (int t = 0; t < 2 * U; ++t) {
+      const uint32_t wu = (t & 1) ? v[t >> 1].w : v[t >> 1].y;
+      acc[t] = accept_f64(wu, w.T, __ldg(w.a + j[t]));
+    }
   }
 #pragma unroll
   for (int u = 0; u < U; ++u) {
@@ -965,7 +978,7 @@ __device__ bool next_item(const Params& p, uint32_t* s_queue, uint32_t q_end, Cl
     w.M = M;
     w.a = reinterpret_cast<const TS*>(p.alpha) + a0;
     w.out = out;
-    w.T = Tc;
+    w.T = item_bound<CMP>(Tc);
     return true;
   }
 }

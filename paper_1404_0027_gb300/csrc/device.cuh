@@ -77,9 +77,74 @@ __device__ __forceinline__ bool accept_f32(uint32_t w, float T, float a) {
   const float u = __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
   return __fmul_rn(u, T) < a;
 }
-__device__ __forceinline__ bool accept_f64(uint32_t w, double T, double a) {
+__device__ __forceinline__ bool accept_f64_exact(uint32_t w, double T, double a) {
   const double u = __dmul_rn(__uint2double_rn(w), 0x1p-32);
   return __dmul_rn(u, T) < a;
+}
+
+// The FP64 test decided in FP32 where that is provably exact.  GB300 runs
+// FP64 arithmetic at a small fraction of its FP32 rate, so a kernel bound by
+// the test's FP64 multiplies first compares in FP32 with margins:
+//   p_f = RN32(RN32(w) Tq), Tq = RN32(T) 2^-32: within 2^-22 of u T (three
+//         roundings; every value is normal when 2^-94 <= T < 2^127);
+//   a_f = alpha, or alpha truncated to FP32 from its bits: within 2^-23 below;
+//   p_f < RN32(a_f (1 - 2^-18)) gives u T < alpha (1 - 2^-19), so
+//         RN64(u T) < alpha: accept;
+//   p_f > RN32(a_f (1 + 2^-18)) gives u T > alpha, so RN64(u T) >= alpha:
+//         reject;
+// alpha = +-0 is rejected (RN64(u T) >= 0).  Trials in between (a relative
+// band of about 2^-17 around the threshold) and propensities outside FP32's
+// normal range (or negative, infinite, NaN) take the FP64 test, so the
+// decision is always that of accept_f64_exact.
+struct F64Bound {
+  double T;
+  float Tq;  // RN32(T) 2^-32 (>= 2^-126) when 2^-94 <= T < 2^127, where the
+             // FP32 margins hold; 0 otherwise (the FP64 test only)
+};
+__device__ __forceinline__ F64Bound f64_bound(double T) {
+  F64Bound b;
+  b.T = T;
+  // the exponent field with the sign bit above it: negatives are not fast
+  const bool fast = ((uint32_t)__double2hiint(T) >> 20) - (1023u - 94u) <= 220u;
+  b.Tq = fast ? __fmul_rn(__double2float_rn(T), 0x1p-32f) : 0.f;
+  return b;
+}
+constexpr float kF64FilterLo = 1.0f - 0x1p-18f;
+constexpr float kF64FilterHi = 1.0f + 0x1p-18f;
+// The pre-filter's FP32 operand: alpha itself (FP32 data) or alpha truncated
+// to FP32 from its bits, when alpha is positive with an exponent in
+// [-125, 127]; 0 for +-0 (never accepted); -1 otherwise (the FP64 test
+// decides).  One register per trial instead of a double.
+__device__ __forceinline__ float f64_filter_operand(double a) {
+  const uint32_t hi = (uint32_t)__double2hiint(a), lo = (uint32_t)__double2loint(a);
+  const uint32_t e = hi >> 20;  // with the sign bit: negatives fail the range check
+  if (e - (1023u - 125u) <= 252u)
+    return __uint_as_float(((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+  return ((hi & 0x7fffffffu) | lo) == 0u ? 0.f : -1.f;
+}
+__device__ __forceinline__ float f64_filter_operand(float a) {
+  const uint32_t bits = __float_as_uint(a);
+  if ((bits >> 23) - 2u <= 252u) return a;  // positive, exponent field in [2, 254]
+  return (bits & 0x7fffffffu) == 0u ? 0.f : -1.f;
+}
+// 1: accept, 0: reject, 2: the FP64 test decides.
+__device__ __forceinline__ int f64_filter(uint32_t w, const F64Bound& t, float af) {
+  if (!(t.Tq > 0.f) || af < 0.f) return 2;
+  if (af == 0.f) return 0;
+  const float pf = __fmul_rn(__uint2float_rn(w), t.Tq);
+  if (pf < __fmul_rn(af, kF64FilterLo)) return 1;
+  if (pf > __fmul_rn(af, kF64FilterHi)) return 0;
+  return 2;
+}
+// The FP64 product out of line: about one trial in 10^5 needs it, and the
+// selection loops that reach it keep their registers.
+static __device__ __noinline__ bool accept_f64_slow(uint32_t w, double T, double a) {
+  return accept_f64_exact(w, T, a);
+}
+template <typename TA>
+__device__ __forceinline__ bool accept_f64(uint32_t w, const F64Bound& t, TA a) {
+  const int d = f64_filter(w, t, f64_filter_operand(a));
+  return d == 2 ? accept_f64_slow(w, t.T, (double)a) : d == 1;
 }
 
 // ---------------------------------------------------------------------------

@@ -162,11 +162,10 @@ __global__ void __launch_bounds__(kNT) k_select(const SelParams p) {
         };
         run_select(U, q, q_end, acc, c);
       } else {
+        const F64Bound tb = f64_bound(T);  // the FP64 test with its FP32 pre-filter
         auto acc = [&](uint32_t j, uint32_t w) -> bool {
-          double a;
-          if constexpr (SMEM) a = (double)s_alpha[j];
-          else a = (double)__ldg(g_alpha + j);
-          return accept_f64(w, T, a);
+          if constexpr (SMEM) return accept_f64(w, tb, s_alpha[j]);
+          else return accept_f64(w, tb, __ldg(g_alpha + j));
         };
         run_select(U, q, q_end, acc, c);
       }

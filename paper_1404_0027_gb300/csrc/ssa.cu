@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
     }
     // ---- bound T = max a (exact, from the comparison copies)
     float Tf = 0.f;
-    double T = 0.0;
+    F64Bound T{};  // the FP64 comparison's bound with its FP32 pre-filter
     bool zero;
     if constexpr (CMP == AR_CMP_F32) {
       const uint32_t tb = warp_max_u32(lmax);
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
       zero = tb == 0u;  // the maximum of non-negative copies, on bit patterns
     } else {
       const unsigned long long tb = warp_max_u64(lmax64);
-      T = __longlong_as_double((long long)tb);
+      T = f64_bound(__longlong_as_double((long long)tb));
       zero = tb == 0ull;
     }
     if (zero) {

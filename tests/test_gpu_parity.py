@@ -96,6 +96,40 @@ def test_select_plain(gb, orc, cmp, fused, dtype):
     _check_select(gb, orc, W.plain_uniform().astype(dtype), 1000, cmp, fused)
 
 
+def _prefilter_vector(dtype):
+    """Propensities over six decades with zeros and values below FP32's normal
+    range (subnormal in the data's own precision too)."""
+    rng = np.random.default_rng(77)
+    if dtype == np.float64:
+        special = [5e-324, 1e-310, 2.0 ** -1022, 2.0 ** -130, 2.0 ** -126, 2.0 ** -125, 0.0, 0.0]
+    else:
+        special = [1e-45, 1e-40, 2.0 ** -127, 2.0 ** -126, 2.0 ** -125, 0.0, 0.0]
+    body = rng.exponential(1.0, 1000) * 10.0 ** rng.uniform(-4, 2, 1000)
+    a = np.concatenate([special, body]).astype(dtype)
+    rng.shuffle(a)
+    return a
+
+
+@pytest.mark.parametrize("fused", [True, False])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_fp64_comparison_prefilter_edges(gb, orc, dtype, fused):
+    """The FP64 comparison decides most trials in FP32 with proven margins and
+    takes the FP64 product within a 2^-17 band of the threshold, for
+    propensities outside FP32's normal range (zeros are rejected outright),
+    and for every trial when the bound lies outside [2^-94, 2^127].  Indices,
+    counters and status equal the oracle's FP64 comparison bit for bit."""
+    a = _prefilter_vector(dtype)
+    _check_select(gb, orc, a, 20_000, 1, fused)                     # T = max
+    if not fused:                                                     # T just above max
+        _check_select(gb, orc, a, 20_000, 1, False,
+                      bound_value=float(a.max()) * (1.0 + 2.0 ** -40))
+    # bounds outside the pre-filter's range: every trial takes the FP64 product
+    scales = (2.0 ** 200, 2.0 ** -300) if dtype == np.float64 else (2.0 ** -110,)
+    for sc in scales:
+        b = (a.astype(np.float64) * sc).astype(dtype)
+        _check_select(gb, orc, b, 5_000, 1, fused)
+
+
 @pytest.mark.parametrize("cmp", [0, 1])
 @pytest.mark.parametrize("K", [1, 33, 4097, 65536])
 def test_select_skewed(gb, orc, cmp, K):
