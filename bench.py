@@ -625,6 +625,12 @@ def main():
     reps = min(K, 3000)
     red_ms = time_alone(bound_only, reps)
     sel_ms = time_alone(select_only, reps)
+
+    def call_fp64(s):  # the whole call with the FP64 comparison (same plans and tiles)
+        gb.ar_select_batched(s["alpha"], s["off"], s["oo"], SEED, 0, b_base, gb.AR_CMP_F64,
+                             1 << 20, s["plan"], s["bs"], s["idx"], s["stats2"], s["st2"],
+                             s["work"], stream)
+    f64_ms = time_alone(call_fp64, min(reps, 1000))
     probes = probe_peaks(dev, stream)
 
     # ---- rooflines ---------------------------------------------------------
@@ -853,6 +859,20 @@ def main():
             e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
+        # the FP64 comparison on the same vector and K
+        g1d = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g1d, stream=stream):
+            call(gb.AR_CMP_F64, K, ix, None)
+        for _ in range(5):
+            g1d.replay()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(reps):
+                g1d.replay()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / reps
         # the inverse transform on the same vector and K (the comparator the
         # paper argues against): exact running sums by a parallel scan, then a
         # bisection per selection
@@ -875,6 +895,8 @@ def main():
         it_ms = e0.elapsed_time(e1) / reps
         blocks = trials / 2.0
         return {"value": K / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms,
+                "fp64_comparison": {"value": K / (ms64 * 1e-3), "unit": UNIT,
+                                    "ms_per_call": ms64},
                 "inverse_transform": {"value": K / (it_ms * 1e-3), "unit": UNIT,
                                       "ms_per_call": it_ms, "status": int(it_st.item()),
                                       "call": "ar_select_it (5 kernels + header memset)"},
@@ -1039,6 +1061,11 @@ def main():
                               fp32_batched_over_fp64_plain_device=value
                               / fp64_plain["device_value"]),
            "single_vector": single,
+           # the batched call with the FP64 comparison, one call at a time
+           # (the FP32 figure beside it: one_call_at_a_time.step_ms_mean)
+           "batched_fp64_comparison": {"value": sel_per_step / (float(f64_ms.mean()) * 1e-3),
+                                       "unit": UNIT, "ms_per_call": float(f64_ms.mean()),
+                                       "fp32_ms_per_call": float(kern_ms.mean())},
            "paper_workload": paper_wl,
            "ssa": ssa,
            "accuracy": {"batched_fp32_vs_fp64": acc_batched,
