@@ -22,7 +22,10 @@
  * - Indices are 0-based.  The rejection sentinel is M (the paper's M+1,
  *   Section "Implementation", made 0-based).
  * - dtype: AR_F32 or AR_F64 propensities.  cmp: AR_CMP_F32 (comparison in
- *   FP32, bulk fast path) or AR_CMP_F64.
+ *   FP32, bulk fast path) or AR_CMP_F64 (the exact FP64 test below; the
+ *   kernels decide it in FP32 wherever proven error margins make that the
+ *   FP64 decision and run the FP64 product for the rest, about one trial in
+ *   10^5, so its results are those of the FP64 test exactly).
  *
  * The random stream (bit-exact contract, Philox4x32-10, Salmon et al. SC'11)
  * -----------------------------------------------------------------------
