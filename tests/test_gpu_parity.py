@@ -233,6 +233,22 @@ def test_batched_wide_range(gb, orc, dtype, plan):
 
 
 @pytest.mark.parametrize("plan", [False, True])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_batched_fp64_comparison_prefilter_edges(gb, orc, dtype, plan):
+    """The batched round's FP64 comparison (FP32 pre-filter, FP64 product near
+    the threshold and outside FP32's range): realizations with subnormal and
+    sub-FP32 propensities and zeros, with bounds inside the pre-filter's range
+    and above 2^127 or below 2^-94 (the FP64 product for every trial), equal
+    the oracle's FP64 comparison bit for bit."""
+    a = _prefilter_vector(dtype)
+    scales = (1.0, 2.0 ** 200, 2.0 ** -300) if dtype == np.float64 else (1.0, 2.0 ** -110)
+    vecs = [(a.astype(np.float64) * sc).astype(dtype) for sc in scales]
+    vecs.append(a[:300].copy())
+    _check_batched(gb, orc, W.batch_from_vectors(vecs, [3000, 700, 450, 1000][:len(vecs)]),
+                   cmp=1, seed=9, sel_offset=5, plan=plan)
+
+
+@pytest.mark.parametrize("plan", [False, True])
 @pytest.mark.parametrize("cmp", [0, 1])
 def test_batched_uneven_small(gb, orc, cmp, plan):
     _check_batched(gb, orc, W.batched_uneven(B=300, seed=301, K=256), cmp=cmp, plan=plan)
