@@ -155,10 +155,20 @@ __device__ __forceinline__ double unfix128(I128 x, int S) {
   return ldexp(v, -S);
 }
 
+// The FP64 comparison of trial word w against alpha_j: the FP32 pre-filter on
+// the operand kept in shared memory, and for the rare trials it leaves open
+// the FP64 test on the state array's value (written by this warp in an
+// earlier step, ordered by the warp's __syncwarp).
+__device__ __forceinline__ bool accept_f64_state(uint32_t w, const F64Bound& T, float op,
+                                                 const double* a, int32_t j) {
+  const int d = f64_filter(w, T, op);
+  return d == 2 ? accept_f64_slow(w, T.T, a[j]) : d == 1;
+}
+
 // XS: the counts live in shared memory during the call (read from and
 // written back to X), when the network is small enough.
 template <int CMP, bool TIMED, bool XS>
-__global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
+__device__ __forceinline__ void ssa_warp(const SsaParams& p) {
   extern __shared__ __align__(16) unsigned char smem[];
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warp = threadIdx.x >> 5;
@@ -167,8 +177,9 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
   // FP32 (or FP64) copies of the propensities for gathers and the bound,
   // then the counts (XS) and the lanes' raised maxima
   unsigned char* wsm = smem + (size_t)warp * p.smem_stride;
+  // FP32 comparison: RN32 copies of the propensities; FP64 comparison: the
+  // FP32 pre-filter's operands (the FP64 values are the state array a)
   float* af = reinterpret_cast<float*>(wsm);
-  double* ad = reinterpret_cast<double*>(af);
   unsigned long long* inc = reinterpret_cast<unsigned long long*>(wsm + p.inc_off);
   uint32_t st = p.status[b];
   if (st & (AR_STATUS_ABSORBED | AR_STATUS_TRIAL_CAP | AR_STATUS_BAD_ALPHA | AR_STATUS_UNSUPPORTED))
@@ -199,7 +210,7 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
       af[r] = f;
       lmax = max(lmax, __float_as_uint(f));
     } else {
-      ad[r] = v;
+      af[r] = f64_filter_operand(v);
       lmax64 = max(lmax64, (unsigned long long)__double_as_longlong(v));
     }
   }
@@ -299,8 +310,8 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
         a0 = 2 * cnt < p.cap && accept_f32(w.y, Tf, af[j0]);
         a1 = !a0 && 2 * cnt + 1 < p.cap && accept_f32(w.w, Tf, af[j1]);
       } else {
-        a0 = 2 * cnt < p.cap && accept_f64(w.y, T, ad[j0]);
-        a1 = !a0 && 2 * cnt + 1 < p.cap && accept_f64(w.w, T, ad[j1]);
+        a0 = 2 * cnt < p.cap && accept_f64_state(w.y, T, af[j0], a, j0);
+        a1 = !a0 && 2 * cnt + 1 < p.cap && accept_f64_state(w.w, T, af[j1], a, j1);
       }
       const uint32_t bal = __ballot_sync(kFull, a0 || a1);
       if (bal) {
@@ -360,11 +371,12 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
             if (fn < fo && __float_as_uint(fo) == om) rescan |= 1u << owner;
             if (fn > fo) atomicMax(inc + owner, (unsigned long long)__float_as_uint(fn));
           } else {
-            const double o = ad[r];
-            ad[r] = vn;
-            if (vn < o && (unsigned long long)__double_as_longlong(o) == om64)
-              rescan |= 1u << owner;
-            if (vn > o) atomicMax(inc + owner, (unsigned long long)__double_as_longlong(vn));
+            // non-negative doubles order as their bit patterns
+            const unsigned long long bo = (unsigned long long)__double_as_longlong(vo);
+            const unsigned long long bn = (unsigned long long)__double_as_longlong(vn);
+            af[r] = f64_filter_operand(vn);
+            if (bn < bo && bo == om64) rescan |= 1u << owner;
+            if (bn > bo) atomicMax(inc + owner, bn);
           }
         }
       }
@@ -384,7 +396,7 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
         if (rescan & (1u << lane)) {
           lmax64 = 0;
           for (int r = lane; r < M; r += 32)
-            lmax64 = max(lmax64, (unsigned long long)__double_as_longlong(ad[r]));
+            lmax64 = max(lmax64, (unsigned long long)__double_as_longlong(a[r]));
         } else {
           lmax64 = max(lmax64, inc[lane]);
         }
@@ -409,6 +421,18 @@ __global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
     if (p.last) p.last[b] = last;
     if (p.trials) p.trials[b] += ntr;
   }
+}
+
+// One warp per realization, FP32 comparison.
+template <bool TIMED, bool XS>
+__global__ void __launch_bounds__(kNTS) k_ssa(const SsaParams p) {
+  ssa_warp<AR_CMP_F32, TIMED, XS>(p);
+}
+// FP64 comparison: held to the FP32 step's four CTAs per SM (64 registers),
+// which its shared memory (FP32 operands only) allows as well.
+template <bool TIMED, bool XS>
+__global__ void __launch_bounds__(kNTS, 4) k_ssa64(const SsaParams p) {
+  ssa_warp<AR_CMP_F64, TIMED, XS>(p);
 }
 
 }  // namespace
@@ -532,8 +556,9 @@ int ssa_launch(const ssa_net* net, int64_t B, int32_t* d_X, double* d_a, double*
       !aligned(d_status, 4) || !aligned(d_last, 4) || !aligned(d_trials, 8))
     return AR_ERR_ALIGN;
   if ((uint64_t)realization_base + (uint64_t)B > (1ull << 32)) return AR_ERR_ARG;
-  // per warp: the comparison copies, the lanes' raised maxima, the counts
-  const size_t es = cmp == AR_CMP_F32 ? 4 : 8;
+  // per warp: the comparison copies (4 bytes each for either comparison), the
+  // lanes' raised maxima, the counts
+  const size_t es = 4;
   const size_t inc_off = ((size_t)net->M * es + 15) & ~size_t(15);
   const size_t x_off = inc_off + 32 * sizeof(unsigned long long);
   const size_t with_x = x_off + (((size_t)net->N * 4 + 15) & ~size_t(15));
@@ -582,19 +607,19 @@ int ssa_launch(const ssa_net* net, int64_t B, int32_t* d_X, double* d_a, double*
   };
   if (cmp == AR_CMP_F32) {
     if (xs) {
-      if (timed) go(k_ssa<AR_CMP_F32, true, true>);
-      else go(k_ssa<AR_CMP_F32, false, true>);
+      if (timed) go(k_ssa<true, true>);
+      else go(k_ssa<false, true>);
     } else {
-      if (timed) go(k_ssa<AR_CMP_F32, true, false>);
-      else go(k_ssa<AR_CMP_F32, false, false>);
+      if (timed) go(k_ssa<true, false>);
+      else go(k_ssa<false, false>);
     }
   } else {
     if (xs) {
-      if (timed) go(k_ssa<AR_CMP_F64, true, true>);
-      else go(k_ssa<AR_CMP_F64, false, true>);
+      if (timed) go(k_ssa64<true, true>);
+      else go(k_ssa64<false, true>);
     } else {
-      if (timed) go(k_ssa<AR_CMP_F64, true, false>);
-      else go(k_ssa<AR_CMP_F64, false, false>);
+      if (timed) go(k_ssa64<true, false>);
+      else go(k_ssa64<false, false>);
     }
   }
   return check_launch();
